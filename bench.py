@@ -1,0 +1,372 @@
+"""Benchmark of the fused FP32 time-stepper on the 16384^2 single-grid
+workload (n0 = 0.35, sigma0 = 4, a = 0.8, chi0 = 1, inoculum bM = 0.71 with
+r0^2 = 32^2, dt = 0.2 x the stability limit).
+
+One benchmark step = `--window` time steps (one fused kernel launch each)
+followed by one diagnostics reduction (masses, invariant, envelope radius).
+The metric is grid-cell updates per second.  Every input is larger than L2
+(3.2 GB read per time step), so no L2 flush is needed between iterations.
+
+Multi-GPU (torchrun): every rank runs its own replica of the grid (the
+workload partitions into independent simulations; no data-path
+collective); the time is the maximum over ranks and the value counts the
+cells of all ranks (weak scaling).
+
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"f32": 20, "f64": 40}  # read b, n, sigma; write b', n'
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--window", type=int, default=100, help="time steps per benchmark step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384, help="grid side")
+    ap.add_argument("--chi0", type=float, default=1.0)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1301_5058_gb300 import workloads as W
+    cfg = dict(W.CONFIG1, nx=args.n, ny=args.n, chi0=args.chi0)
+    return cfg
+
+
+def config_block(args, cfg):
+    return {"workload": f"single grid {cfg['nx']}x{cfg['ny']} {args.precision} state, "
+                        f"n0={cfg['n0']} sigma0={cfg['sigma0']} a={cfg['noise_amp']} "
+                        f"chi0={cfg['chi0']} receptor law, static uniform noise, forward Euler, "
+                        f"dt=0.2 x limit",
+            "nx": cfg["nx"], "ny": cfg["ny"], "time_steps_per_step": args.window,
+            "diagnostics_per_step": 1,
+            "l2": "inputs larger than L2 (3 fields x 1 GiB read per time step); no flush",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def step_kernel_traffic(prec):
+    """ncu DRAM bytes per launch of the step kernel, if recorded for the
+    current kernel source (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc", "cx_step.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec.get(prec, {}).get("dram_bytes_per_launch_16384sq")
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons, taken during
+    the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1301_5058_gb300 as cx
+    from paper_1301_5058_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = workload(args)
+    grid, params, seed = W.split(cfg)
+    params["precision"] = cx.CX_PREC_F32 if args.precision == "f32" else cx.CX_PREC_F64
+    seed = seed + rank
+    sim = cx.Sim(grid["nx"], grid["ny"], grid["dx"], seed=seed, **params)
+    stream = torch.cuda.current_stream(dev)
+    cx.cx_set_stream(sim.h, stream.cuda_stream)
+    cells = cfg["nx"] * cfg["ny"]
+    K, Wm, S = args.steps, args.warmup, args.window
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def bench_step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        cx.cx_step(sim.h, S)
+        if ev is not None:
+            ev[1].record(stream)
+        return cx.cx_diagnostics(sim.h)
+
+    for _ in range(Wm):
+        bench_step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+    with ClockSampler(gpu_id) as clk:
+        start.record(stream)
+        for k in range(K):
+            d = bench_step(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed = start.elapsed_time(stop) / 1e3
+    kernel_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    per_launch = kernel_s / (K * S)
+
+    # end to end through the C ABI with host buffers: every step uploads its
+    # inputs (b, n) from pinned host memory and reads the diagnostics back
+    e2e = None
+    if not args.no_e2e:
+        np_dtype = np.float32 if args.precision == "f32" else np.float64
+        host_dtype = cx.CX_F32 if args.precision == "f32" else cx.CX_F64
+        hb = torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float32 if np_dtype == np.float32 else torch.float64,
+                         pin_memory=True)
+        hn = torch.empty_like(hb, pin_memory=True)
+        cx.cx_get_field(sim.h, cx.CX_FIELD_B, hb.numpy())
+        cx.cx_get_field(sim.h, cx.CX_FIELD_N, hn.numpy())
+        L = cx.lib()
+
+        def e2e_step():
+            cx._check(L.cx_set_field(sim.h, cx.CX_FIELD_B, ctypes.c_void_p(hb.data_ptr()), host_dtype, cells))
+            cx._check(L.cx_set_field(sim.h, cx.CX_FIELD_N, ctypes.c_void_p(hn.data_ptr()), host_dtype, cells))
+            cx.cx_step(sim.h, S)
+            return cx.cx_diagnostics(sim.h)
+
+        for _ in range(max(1, Wm)):
+            e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"seconds": e2e_s,
+               "h2d_bytes_per_step": 2 * cells * hb.element_size(),
+               "d2h_bytes_per_step": ctypes.sizeof(cx.cx_diag) + 64}
+    diag = d.as_dict()
+    sim.close()
+    return {"elapsed": elapsed, "kernel_s": kernel_s, "per_launch": per_launch, "cells": cells,
+            "clocks": clk.summary(), "e2e": e2e, "diag": diag, "cfg": cfg}
+
+
+def cpu_baseline_sample(cfg, side=4096, steps=8):
+    """Time the FP64 oracle (single thread, as it stands) on the central
+    side x side window of the workload for `steps` time steps."""
+    import oracle
+    # same parameters and noise law; the inoculum sits at the window's centre
+    s = oracle.sigma_field(side, side, cfg["seed"], cfg["sigma0"], cfg["noise_amp"])
+    b, n = oracle.initial_state(side, side, cfg["dx"], cfg["n0"], cfg["bM"], cfg["r0sq"])
+    dt = cfg["cfl_frac"] * oracle.dt_limit(dx=cfg["dx"], Dn=cfg["Dn"], theta=cfg["theta"],
+                                           chi0=cfg["chi0"], n0=cfg["n0"], bM=cfg["bM"],
+                                           sigma0=cfg["sigma0"], amp=cfg["noise_amp"])
+    t0 = time.perf_counter()
+    oracle.run(s, b, n, steps, dx=cfg["dx"], dt=dt, Dn=cfg["Dn"], theta=cfg["theta"],
+               chi0=cfg["chi0"])
+    sec = time.perf_counter() - t0
+    return side * side * steps / sec, sec, \
+        f"central {side}x{side} window of the workload, {steps} FP64 oracle steps ({sec:.1f} s)"
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return main_reference(args, rank, world)
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    r = run_ours(args, rank, world, local_rank)
+
+    elapsed, e2e_s = r["elapsed"], (r["e2e"] or {}).get("seconds")
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([elapsed, e2e_s or 0.0, r["per_launch"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed, e2e_s, per_launch = (float(v) for v in t.tolist())
+    else:
+        per_launch = r["per_launch"]
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    cfg, cells = r["cfg"], r["cells"]
+    K, S = args.steps, args.window
+    units = cells * S * K * world
+    value = units / elapsed
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL[args.precision] * cells / per_launch / 1e9
+    out = {
+        "metric": "grid-cell updates/s",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed / K * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.precision,
+        "data": "synthetic (seeded sigma field and Gaussian inoculum)",
+        "config": config_block(args, cfg),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": step_kernel_traffic(args.precision),
+                     "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision],
+                     "kernel_ms_per_launch": per_launch * 1e3},
+        "gpu_launches": K * (S + 2),
+        "clocks": r["clocks"],
+        "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b", "min_n")},
+    }
+    if r["e2e"]:
+        out["e2e"] = {"value": units / e2e_s, "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": r["e2e"]["h2d_bytes_per_step"],
+                      "d2h_bytes_per_step": r["e2e"]["d2h_bytes_per_step"]}
+    if not args.no_cpu_baseline and world == 1:
+        v, sec, sample = cpu_baseline_sample(cfg)
+        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                               "sample": sample}
+    print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, each step one
+    oracle time step on the central 4096^2 window of the same workload."""
+    if rank != 0:
+        return
+    cfg = workload(args)
+    import oracle
+    side = min(4096, cfg["nx"])
+    s = oracle.sigma_field(side, side, cfg["seed"], cfg["sigma0"], cfg["noise_amp"])
+    b, n = oracle.initial_state(side, side, cfg["dx"], cfg["n0"], cfg["bM"], cfg["r0sq"])
+    dt = cfg["cfl_frac"] * oracle.dt_limit(dx=cfg["dx"], Dn=cfg["Dn"], theta=cfg["theta"],
+                                           chi0=cfg["chi0"], n0=cfg["n0"], bM=cfg["bM"],
+                                           sigma0=cfg["sigma0"], amp=cfg["noise_amp"])
+    kw = dict(dx=cfg["dx"], dt=dt, Dn=cfg["Dn"], theta=cfg["theta"], chi0=cfg["chi0"])
+    for _ in range(args.warmup):
+        b, n = oracle.step(s, b, n, **kw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b, n = oracle.step(s, b, n, **kw)
+    sec = time.perf_counter() - t0
+    value = side * side * args.steps / sec
+    sample = f"central {side}x{side} window of the workload, one FP64 oracle step per benchmark step"
+    print(json.dumps({
+        "impl": "reference", "metric": "grid-cell updates/s", "value": value,
+        "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(args, cfg),
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * cx.h -- C ABI of the GB300 time-stepper for the bacteria/nutrient
+ * chemotaxis system with degenerate cross diffusion (Leyva, Malaga & Plaza).
+ *
+ * The library integrates, on one GPU, the dimensionless system of
+ * Sec. 2.4 (Eq. ka-chem-model), written in its general form with the
+ * nutrient diffusivity Dn and conversion factor theta of Eq. ka-model-dim:
+ *
+ *   n_t = Dn Lap(n) - n b                                        (Eq. eqnadim)
+ *   b_t = div(sigma n b grad b) + theta n b
+ *         - div(chi(n) sigma n b^2 grad n)                       (Eq. eqbadim)
+ *   chi(n) = chi0 / (1 + n)^2   (receptor law, Eq. receptor_law)
+ *         or chi0               (constant law, Eq. velo-system)
+ *   sigma  = sigma0 (1 + a Delta)                                (Eq. CoefCrsDif)
+ *
+ * on an nx*ny cell-centred grid of spacing dx with no-flux walls
+ * (Eq. bconds), initial data n = n0 and b = bM exp(-r^2/r0sq) (Eq. inicond,
+ * Eq. inibacexp), by explicit finite volumes (face fluxes with arithmetic
+ * face means) and forward Euler or Heun time stepping (Sec. 3).
+ *
+ * Conventions for every call:
+ *   - return CX_OK (0) on success, a negative CX_ERR_* code on failure; no
+ *     call throws and no call aborts the process;
+ *   - cx_last_error() returns a message for the last failure on the
+ *     calling thread;
+ *   - handles own every device buffer they allocate; the caller owns every
+ *     host pointer it passes and may reuse it when the call returns;
+ *   - host arrays are row-major: element (i, j) is at [j*nx + i], i along x;
+ *   - NULL handles are rejected with CX_ERR_INVALID_ARG (cx_destroy and
+ *     cx_batch_destroy accept NULL and do nothing).
+ */
+#ifndef CX_H
+#define CX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CX_VERSION 1
+
+/* status codes */
+#define CX_OK 0
+#define CX_ERR_INVALID_ARG (-1)  /* bad pointer, size, enum or parameter value */
+#define CX_ERR_DT_UNSTABLE (-2)  /* dt above the explicit stability limit */
+#define CX_ERR_OOM (-3)          /* device or pinned-host allocation failed */
+#define CX_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define CX_ERR_NONFINITE (-5)    /* diagnostics found a NaN or Inf */
+#define CX_ERR_NEGATIVE (-6)     /* diagnostics found b < 0 or n < 0 */
+#define CX_ERR_TIMEOUT (-7)      /* a bounded device-side wait ran out */
+#define CX_ERR_IO (-8)           /* checkpoint file could not be read/written */
+#define CX_ERR_UNSUPPORTED (-9)  /* option combination not built */
+
+/* field selectors */
+#define CX_FIELD_B 0
+#define CX_FIELD_N 1
+#define CX_FIELD_SIGMA 2
+
+/* host element types for field I/O */
+#define CX_F64 0
+#define CX_F32 1
+
+/* option values */
+#define CX_CHEMO_RECEPTOR 0   /* chi0 / (1+n)^2 at the face */
+#define CX_CHEMO_CONSTANT 1   /* chi0 */
+#define CX_MOBILITY_CENTRAL 0 /* b^2 at a face = ((b_L+b_R)/2)^2 */
+#define CX_MOBILITY_UPWIND 1  /* b^2 at a face = b^2 of the lower-n cell */
+#define CX_NOISE_UNIFORM 0    /* Delta uniform on [-1,1) */
+#define CX_NOISE_TRIANGULAR 1 /* Delta triangular on (-1,1) (Sec. 3) */
+#define CX_NOISE_STATIC 0     /* sigma drawn once, at time step 0 */
+#define CX_NOISE_PER_STEP 1   /* sigma redrawn for every time step (Sec. 3) */
+#define CX_SCHEME_EULER 0     /* u' = u + dt r(u) */
+#define CX_SCHEME_HEUN 1      /* u' = u + dt/2 (r(u) + r(u + dt r(u))) */
+#define CX_PREC_F64 0         /* state and arithmetic in FP64 */
+#define CX_PREC_F32 1         /* state and arithmetic in FP32; diagnostics in FP64 */
+
+typedef struct cx_ctx cx_ctx;     /* one simulation; owns its device buffers */
+typedef struct cx_batch cx_batch; /* many independent simulations */
+
+/* Grid: nx*ny cells of side dx.  Cell (i,j) has its centre at
+ * x = (i + 1/2 - nx/2) dx, y = (j + 1/2 - ny/2) dx (inoculum at the origin). */
+typedef struct {
+    int32_t nx, ny;
+    double dx;
+} cx_grid;
+
+/* Model and numerical parameters (Sec. 2.4 free parameters sigma0, n0,
+ * chi0; Dn and theta of Eq. ka-model-dim, 1 in the normalised form). */
+typedef struct {
+    double n0;          /* initial nutrient level (Eq. inicond) */
+    double chi0;        /* chemotactic strength, >= 0 */
+    double sigma0;      /* mean motility (agar softness), >= 0 */
+    double noise_amp;   /* a in sigma = sigma0 (1 + a Delta), 0 <= a <= 1 */
+    double Dn;          /* nutrient diffusivity, >= 0 */
+    double theta;       /* conversion factor, >= 0 */
+    double bM;          /* inoculum peak (Eq. inibacexp) */
+    double r0sq;        /* inoculum width: b = bM exp(-r^2 / r0sq), > 0 */
+    double dt;          /* time step; 0 selects cfl_frac * cx_dt_limit() */
+    double cfl_frac;    /* fraction of the limit used when dt == 0, (0, 1] */
+    double b_threshold; /* envelope level for r_env; <= 0 selects 0.1 theta n0 */
+    int32_t chemo_law;  /* CX_CHEMO_* */
+    int32_t mobility;   /* CX_MOBILITY_* */
+    int32_t noise_dist; /* CX_NOISE_UNIFORM / CX_NOISE_TRIANGULAR */
+    int32_t noise_mode; /* CX_NOISE_STATIC / CX_NOISE_PER_STEP */
+    int32_t scheme;     /* CX_SCHEME_* */
+    int32_t precision;  /* CX_PREC_* */
+} cx_params;
+
+/* Diagnostics of the current state (every sum accumulated in FP64). */
+typedef struct {
+    int64_t step;     /* time steps taken */
+    double t;         /* step * dt */
+    double dt;
+    double mass_b;    /* dx^2 sum b */
+    double mass_n;    /* dx^2 sum n */
+    double invariant; /* dx^2 sum (b + theta n): conserved (Eq. mass-conser) */
+    double min_b, min_n, max_b;
+    double r_env;     /* largest cell-centre distance with b >= b_threshold, 0 if none */
+    int32_t finite;   /* 1 if every b and n is finite */
+    int32_t status;   /* CX_OK, CX_ERR_NONFINITE or CX_ERR_NEGATIVE */
+} cx_diag;
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------- */
+
+/* Library version (CX_VERSION of the build). */
+int cx_version(void);
+
+/* Static text for a status code; never NULL. */
+const char *cx_strerror(int code);
+
+/* Message of the last failure on this thread ("" if none); valid until the
+ * next failing call on the same thread. */
+const char *cx_last_error(void);
+
+/* Fill *p with the normalised model (Dn = theta = 1), receptor law, central
+ * mobility, static uniform noise a = 0.5, Euler, FP32, dt = 0.2 x limit,
+ * n0 = 0.71, sigma0 = 1, chi0 = 0, bM = 0.71, r0sq = 6.25 (Sec. 3). */
+int cx_params_default(cx_params *p);
+
+/* Explicit stability limit for (g, p) (Sec. 3 only states that its steps
+ * were stable; this library's reading):
+ *   B = bM + theta n0,  Dmax = max(Dn, sigma0 (1+a) n0 B (1 + chi0 B)),
+ *   limit = min(dx^2 / (4 Dmax), 1 / (4 Dn / dx^2 + B)).
+ * Validates g and p; writes *limit. */
+int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit);
+
+/* ---- one simulation ------------------------------------------------------ */
+
+/* Allocate a simulation on the current CUDA device, draw sigma from
+ * Philox4x32-10 keyed by `seed` (cell index and time step as counter;
+ * Salmon et al., SC'11) and set the initial state.  Synchronous.
+ * Errors: INVALID_ARG (bad grid/params/out), DT_UNSTABLE (p->dt above the
+ * limit), OOM, CUDA.  On error *out is left NULL. */
+int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out);
+
+/* Run all later work of `c` on `stream` (a cudaStream_t, e.g. a torch
+ * stream handle; NULL = the legacy default stream). */
+int cx_set_stream(cx_ctx *c, void *stream);
+
+/* Advance by n_steps >= 0 time steps.  Asynchronous on the handle's stream:
+ * kernel launches only, no host synchronisation.  Errors: INVALID_ARG, CUDA
+ * (launch failures). */
+int cx_step(cx_ctx *c, int64_t n_steps);
+
+/* Wait for all queued work of the handle. */
+int cx_synchronize(cx_ctx *c);
+
+/* Reduce the current state (FP64 sums, deterministic order) and copy the
+ * result to *out.  Synchronises the handle's stream.  Returns CX_OK, or
+ * CX_ERR_NONFINITE / CX_ERR_NEGATIVE with *out filled when the state is
+ * unhealthy, or INVALID_ARG / CUDA. */
+int cx_diagnostics(cx_ctx *c, cx_diag *out);
+
+/* Copy field `which` (CX_FIELD_*) to the host array `host` of `count`
+ * elements (count must equal nx*ny) of type `dtype` (CX_F64/CX_F32),
+ * converting if the state precision differs.  Synchronous. */
+int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t count);
+
+/* Overwrite field `which` from a host array (same layout rules as
+ * cx_get_field).  Synchronous with respect to `host`.  Replacing sigma is
+ * allowed only with CX_NOISE_STATIC (per-step noise regenerates it). */
+int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size_t count);
+
+/* Copy the handle's grid, parameters (with dt resolved) and seed; any
+ * output pointer may be NULL. */
+int cx_get_config(cx_ctx *c, cx_grid *g, cx_params *p, uint64_t *seed);
+
+/* Current step count, time and time step. */
+int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt);
+
+/* Reset the step counter (the time is step * dt); used with cx_set_field to
+ * restart from given data. */
+int cx_set_step(cx_ctx *c, int64_t step);
+
+/* Number of time steps fused per launch (temporal blocking depth), 1..8.
+ * Results do not depend on it bit for bit.  Default chosen per grid. */
+int cx_set_time_block(cx_ctx *c, int32_t k);
+int cx_get_time_block(cx_ctx *c, int32_t *k);
+
+/* Write / read a checkpoint: header (grid, params, seed, step, dt,
+ * precision) and the raw b, n and sigma arrays.  A run resumed from a
+ * checkpoint continues bit for bit as the uninterrupted run.  Errors: IO,
+ * INVALID_ARG, OOM, CUDA. */
+int cx_save(cx_ctx *c, const char *path);
+int cx_load(const char *path, cx_ctx **out);
+
+/* Free the handle and its device buffers.  NULL is a no-op. */
+void cx_destroy(cx_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CX_H */

@@ -1,0 +1,295 @@
+"""Python binding of libcx.so, the GB300 time-stepper for the bacteria /
+nutrient chemotaxis system with degenerate cross diffusion (Leyva, Malaga &
+Plaza, Eq. ka-chem-model).
+
+This module only marshals arguments: every step of the method runs in the
+library's CUDA kernels.  The functions keep the C names of include/cx.h and
+raise ``CxError`` on a non-zero status.  ``Sim`` is a small convenience
+wrapper over one handle.  There is no CPU fallback: if libcx.so is missing,
+importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcx.so")
+
+# status codes, field selectors and options (include/cx.h)
+CX_OK = 0
+CX_ERR_INVALID_ARG = -1
+CX_ERR_DT_UNSTABLE = -2
+CX_ERR_OOM = -3
+CX_ERR_CUDA = -4
+CX_ERR_NONFINITE = -5
+CX_ERR_NEGATIVE = -6
+CX_ERR_TIMEOUT = -7
+CX_ERR_IO = -8
+CX_ERR_UNSUPPORTED = -9
+CX_FIELD_B, CX_FIELD_N, CX_FIELD_SIGMA = 0, 1, 2
+CX_F64, CX_F32 = 0, 1
+CX_CHEMO_RECEPTOR, CX_CHEMO_CONSTANT = 0, 1
+CX_MOBILITY_CENTRAL, CX_MOBILITY_UPWIND = 0, 1
+CX_NOISE_UNIFORM, CX_NOISE_TRIANGULAR = 0, 1
+CX_NOISE_STATIC, CX_NOISE_PER_STEP = 0, 1
+CX_SCHEME_EULER, CX_SCHEME_HEUN = 0, 1
+CX_PREC_F64, CX_PREC_F32 = 0, 1
+
+
+class cx_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double)]
+
+
+class cx_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("n0", "chi0", "sigma0", "noise_amp", "Dn", "theta", "bM", "r0sq", "dt",
+                 "cfl_frac", "b_threshold")] + \
+               [(k, ctypes.c_int32) for k in
+                ("chemo_law", "mobility", "noise_dist", "noise_mode", "scheme", "precision")]
+
+
+class cx_diag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64)] + \
+               [(k, ctypes.c_double) for k in
+                ("t", "dt", "mass_b", "mass_n", "invariant", "min_b", "min_n", "max_b", "r_env")] + \
+               [("finite", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+# every entry point of include/cx.h with its ctypes signature
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "cx_version": (ctypes.c_int, []),
+    "cx_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "cx_last_error": (ctypes.c_char_p, []),
+    "cx_params_default": (ctypes.c_int, [ctypes.POINTER(cx_params)]),
+    "cx_dt_limit": (ctypes.c_int, [ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "cx_create": (ctypes.c_int, [ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
+                                 ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "cx_set_stream": (ctypes.c_int, [_P, _P]),
+    "cx_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cx_synchronize": (ctypes.c_int, [_P]),
+    "cx_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(cx_diag)]),
+    "cx_get_field": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_size_t]),
+    "cx_set_field": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_size_t]),
+    "cx_get_config": (ctypes.c_int, [_P, ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "cx_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "cx_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cx_set_time_block": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cx_get_time_block": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "cx_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "cx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "cx_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libcx.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with "
+                          "paper_1301_5058_gb300._build.build() (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != CX_OK:
+        raise CxError(rc, lib().cx_last_error().decode() or lib().cx_strerror(rc).decode())
+    return rc
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+def cx_version() -> int:
+    return lib().cx_version()
+
+
+def cx_strerror(code: int) -> str:
+    return lib().cx_strerror(code).decode()
+
+
+def cx_last_error() -> str:
+    return lib().cx_last_error().decode()
+
+
+def cx_params_default(**overrides) -> cx_params:
+    p = cx_params()
+    _check(lib().cx_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"cx_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def cx_dt_limit(grid: cx_grid, params: cx_params) -> float:
+    v = ctypes.c_double()
+    _check(lib().cx_dt_limit(ctypes.byref(grid), ctypes.byref(params), ctypes.byref(v)))
+    return v.value
+
+
+def cx_create(grid: cx_grid, params: cx_params, seed: int) -> int:
+    h = _P()
+    _check(lib().cx_create(ctypes.byref(grid), ctypes.byref(params), seed, ctypes.byref(h)))
+    return h.value
+
+
+def cx_set_stream(h, stream: int):
+    _check(lib().cx_set_stream(h, stream))
+
+
+def cx_step(h, n_steps: int):
+    _check(lib().cx_step(h, n_steps))
+
+
+def cx_synchronize(h):
+    _check(lib().cx_synchronize(h))
+
+
+def cx_diagnostics(h, check: bool = True) -> cx_diag:
+    d = cx_diag()
+    rc = lib().cx_diagnostics(h, ctypes.byref(d))
+    if check:
+        _check(rc)
+    elif rc not in (CX_OK, CX_ERR_NONFINITE, CX_ERR_NEGATIVE):
+        _check(rc)
+    return d
+
+
+def _host_view(arr: np.ndarray):
+    if arr.dtype == np.float64:
+        return CX_F64
+    if arr.dtype == np.float32:
+        return CX_F32
+    raise TypeError("host arrays must be float64 or float32")
+
+
+def cx_get_field(h, which: int, out: np.ndarray) -> np.ndarray:
+    """Copy a field into the C-contiguous host array `out` (float64/float32)."""
+    if not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be C-contiguous")
+    _check(lib().cx_get_field(h, which, out.ctypes.data, _host_view(out), out.size))
+    return out
+
+
+def cx_set_field(h, which: int, src: np.ndarray):
+    src = np.ascontiguousarray(src)
+    _check(lib().cx_set_field(h, which, src.ctypes.data, _host_view(src), src.size))
+
+
+def cx_get_config(h):
+    g, p, seed = cx_grid(), cx_params(), ctypes.c_uint64()
+    _check(lib().cx_get_config(h, ctypes.byref(g), ctypes.byref(p), ctypes.byref(seed)))
+    return g, p, seed.value
+
+
+def cx_get_time(h):
+    s, t, dt = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().cx_get_time(h, ctypes.byref(s), ctypes.byref(t), ctypes.byref(dt)))
+    return s.value, t.value, dt.value
+
+
+def cx_set_step(h, step: int):
+    _check(lib().cx_set_step(h, step))
+
+
+def cx_set_time_block(h, k: int):
+    _check(lib().cx_set_time_block(h, k))
+
+
+def cx_get_time_block(h) -> int:
+    k = ctypes.c_int32()
+    _check(lib().cx_get_time_block(h, ctypes.byref(k)))
+    return k.value
+
+
+def cx_save(h, path: str):
+    _check(lib().cx_save(h, os.fsencode(path)))
+
+
+def cx_load(path: str) -> int:
+    h = _P()
+    _check(lib().cx_load(os.fsencode(path), ctypes.byref(h)))
+    return h.value
+
+
+def cx_destroy(h):
+    if h:
+        lib().cx_destroy(h)
+
+
+# ---- convenience wrapper -----------------------------------------------------
+
+class Sim:
+    """One simulation handle.  ``Sim(nx, ny, dx=1.0, seed=0, **params)``."""
+
+    def __init__(self, nx, ny, dx=1.0, seed=0, handle=None, **params):
+        self.grid = cx_grid(nx, ny, dx)
+        self.params = cx_params_default(**params)
+        self.h = handle if handle is not None else cx_create(self.grid, self.params, seed)
+
+    @classmethod
+    def load(cls, path):
+        h = cx_load(path)
+        obj = cls.__new__(cls)
+        obj.h = h
+        obj.grid, obj.params, _ = cx_get_config(h)
+        return obj
+
+    def step(self, n):
+        cx_step(self.h, n)
+
+    def diagnostics(self, check=True) -> dict:
+        return cx_diagnostics(self.h, check=check).as_dict()
+
+    def field(self, which, dtype=np.float64):
+        ny, nx = self.shape
+        return cx_get_field(self.h, which, np.empty((ny, nx), dtype))
+
+    def set_field(self, which, arr):
+        cx_set_field(self.h, which, arr)
+
+    @property
+    def shape(self):
+        return (self.grid.ny, self.grid.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

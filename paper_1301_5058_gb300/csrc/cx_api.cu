@@ -1,0 +1,591 @@
+// cx_api.cu -- the C ABI declared in include/cx.h: parameter validation, the
+// stability limit, buffer ownership, time stepping, diagnostics, field I/O
+// and checkpoints.  Every step of the method runs in the library's kernels;
+// this file only allocates, launches and copies.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cx_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(CX_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(CX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CX_CUDA(call, what)                                     \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));    \
+    } while (0)
+
+bool finite_nonneg(double v) { return isfinite(v) && v >= 0.0; }
+
+int validate(const cx_grid *g, const cx_params *p)
+{
+    if (!g || !p) return fail(CX_ERR_INVALID_ARG, "grid and params must not be NULL");
+    if (g->nx < 1 || g->ny < 1)
+        return fail(CX_ERR_INVALID_ARG, "grid %d x %d: both sides must be >= 1", g->nx, g->ny);
+    if ((long long)g->nx * g->ny > (1LL << 32))
+        return fail(CX_ERR_INVALID_ARG, "grid %d x %d exceeds 2^32 cells", g->nx, g->ny);
+    if (g->ny > 65535LL * 32)
+        return fail(CX_ERR_INVALID_ARG, "ny = %d exceeds %d", g->ny, 65535 * 32);
+    if (!(isfinite(g->dx) && g->dx > 0.0))
+        return fail(CX_ERR_INVALID_ARG, "dx must be finite and > 0");
+    const struct { const char *name; double v; } nonneg[] = {
+        {"n0", p->n0}, {"chi0", p->chi0}, {"sigma0", p->sigma0}, {"noise_amp", p->noise_amp},
+        {"Dn", p->Dn}, {"theta", p->theta}, {"bM", p->bM}, {"dt", p->dt},
+    };
+    for (const auto &q : nonneg)
+        if (!finite_nonneg(q.v))
+            return fail(CX_ERR_INVALID_ARG, "%s = %g must be finite and >= 0", q.name, q.v);
+    if (p->noise_amp > 1.0)
+        return fail(CX_ERR_INVALID_ARG, "noise_amp = %g must be <= 1 (sigma >= 0)", p->noise_amp);
+    if (!(isfinite(p->r0sq) && p->r0sq > 0.0))
+        return fail(CX_ERR_INVALID_ARG, "r0sq must be finite and > 0");
+    if (p->dt == 0.0 && !(isfinite(p->cfl_frac) && p->cfl_frac > 0.0 && p->cfl_frac <= 1.0))
+        return fail(CX_ERR_INVALID_ARG, "cfl_frac = %g must lie in (0, 1]", p->cfl_frac);
+    if (!isfinite(p->b_threshold))
+        return fail(CX_ERR_INVALID_ARG, "b_threshold must be finite");
+    if (p->chemo_law != CX_CHEMO_RECEPTOR && p->chemo_law != CX_CHEMO_CONSTANT)
+        return fail(CX_ERR_INVALID_ARG, "chemo_law = %d", p->chemo_law);
+    if (p->mobility != CX_MOBILITY_CENTRAL && p->mobility != CX_MOBILITY_UPWIND)
+        return fail(CX_ERR_INVALID_ARG, "mobility = %d", p->mobility);
+    if (p->noise_dist != CX_NOISE_UNIFORM && p->noise_dist != CX_NOISE_TRIANGULAR)
+        return fail(CX_ERR_INVALID_ARG, "noise_dist = %d", p->noise_dist);
+    if (p->noise_mode != CX_NOISE_STATIC && p->noise_mode != CX_NOISE_PER_STEP)
+        return fail(CX_ERR_INVALID_ARG, "noise_mode = %d", p->noise_mode);
+    if (p->scheme != CX_SCHEME_EULER && p->scheme != CX_SCHEME_HEUN)
+        return fail(CX_ERR_INVALID_ARG, "scheme = %d", p->scheme);
+    if (p->precision != CX_PREC_F64 && p->precision != CX_PREC_F32)
+        return fail(CX_ERR_INVALID_ARG, "precision = %d", p->precision);
+    return CX_OK;
+}
+
+double dt_limit_of(const cx_grid *g, const cx_params *p)
+{
+    const double B = p->bM + p->theta * p->n0;
+    const double sigma_max = p->sigma0 * (1.0 + p->noise_amp);
+    const double dchem = sigma_max * p->n0 * B * (1.0 + p->chi0 * B);
+    const double dmax = p->Dn > dchem ? p->Dn : dchem;
+    const double dx2 = g->dx * g->dx;
+    const double l1 = dx2 / (4.0 * dmax);
+    const double l2 = 1.0 / (4.0 * p->Dn / dx2 + B);
+    return l1 < l2 ? l1 : l2;
+}
+
+double b_threshold_of(const cx_params *p)
+{
+    return p->b_threshold > 0.0 ? p->b_threshold : 0.1 * p->theta * p->n0;
+}
+
+cx::Coef coef_of(const cx_ctx *c)
+{
+    const double dx2 = c->g.dx * c->g.dx;
+    cx::Coef k;
+    k.cA = c->dt / (8.0 * dx2);
+    k.cChi = c->p.chemo_law == CX_CHEMO_RECEPTOR ? 2.0 * c->p.chi0 : 0.5 * c->p.chi0;
+    k.cG = c->dt * c->p.Dn / dx2;
+    k.cR = c->dt * c->p.theta;
+    k.cN = c->dt;
+    return k;
+}
+
+void free_buffers(cx_ctx *c)
+{
+    for (int q = 0; q < 2; ++q) {
+        if (c->b[q]) cudaFree(c->b[q]);
+        if (c->n[q]) cudaFree(c->n[q]);
+        c->b[q] = c->n[q] = nullptr;
+    }
+    if (c->sigma) cudaFree(c->sigma);
+    if (c->diag.partials) cudaFree(c->diag.partials);
+    if (c->diag.result) cudaFree(c->diag.result);
+    if (c->h_diag) cudaFreeHost(c->h_diag);
+    c->sigma = nullptr;
+    c->diag.partials = c->diag.result = nullptr;
+    c->h_diag = nullptr;
+}
+
+// Allocate the handle and its buffers (contents: zero).
+int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx_ctx **out)
+{
+    cx_ctx *c = new (std::nothrow) cx_ctx;
+    if (!c) return fail(CX_ERR_OOM, "host allocation of the handle failed");
+    memset(c, 0, sizeof *c);
+    c->g = *g;
+    c->p = *p;
+    c->seed = seed;
+    c->prec = p->precision;
+    c->elem = c->prec == CX_PREC_F64 ? sizeof(double) : sizeof(float);
+    const long long align = 128 / (long long)c->elem;  // rows start on 128-byte lines
+    c->pitch = ((long long)g->nx + align - 1) / align * align;
+    c->dt = dt;
+    c->time_block = 1;
+    c->stream = nullptr;
+    cudaGetDevice(&c->device);
+    const size_t bytes = (size_t)c->pitch * (size_t)g->ny * c->elem;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaMalloc(&c->b[q], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->n[q], bytes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->sigma, bytes);
+    c->diag.blocks = cx::diag_blocks_for(g->ny);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->diag.partials, 8 * sizeof(double) * c->diag.blocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->diag.result, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_diag, 8 * sizeof(double));
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaMemset(c->b[q], 0, bytes);
+        if (e == cudaSuccess) e = cudaMemset(c->n[q], 0, bytes);
+    }
+    if (e == cudaSuccess) e = cudaMemset(c->sigma, 0, bytes);
+    if (e != cudaSuccess) {
+        free_buffers(c);
+        delete c;
+        cudaGetLastError();  // clear a sticky allocation error
+        return cuda_fail(e, "device allocation");
+    }
+    *out = c;
+    return CX_OK;
+}
+
+int check_ctx(const cx_ctx *c)
+{
+    if (!c) return fail(CX_ERR_INVALID_ARG, "NULL handle");
+    return CX_OK;
+}
+
+void *field_ptr(cx_ctx *c, int which)
+{
+    if (which == CX_FIELD_B) return c->b[c->cur];
+    if (which == CX_FIELD_N) return c->n[c->cur];
+    return c->sigma;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cx_version(void) { return CX_VERSION; }
+
+const char *cx_strerror(int code)
+{
+    switch (code) {
+    case CX_OK: return "ok";
+    case CX_ERR_INVALID_ARG: return "invalid argument";
+    case CX_ERR_DT_UNSTABLE: return "time step above the explicit stability limit";
+    case CX_ERR_OOM: return "out of memory";
+    case CX_ERR_CUDA: return "CUDA error";
+    case CX_ERR_NONFINITE: return "non-finite value in the state";
+    case CX_ERR_NEGATIVE: return "negative density in the state";
+    case CX_ERR_TIMEOUT: return "device-side wait timed out";
+    case CX_ERR_IO: return "checkpoint I/O error";
+    case CX_ERR_UNSUPPORTED: return "unsupported option combination";
+    default: return "unknown status code";
+    }
+}
+
+const char *cx_last_error(void) { return g_err; }
+
+int cx_params_default(cx_params *p)
+{
+    if (!p) return fail(CX_ERR_INVALID_ARG, "params must not be NULL");
+    memset(p, 0, sizeof *p);
+    p->n0 = 0.71;
+    p->chi0 = 0.0;
+    p->sigma0 = 1.0;
+    p->noise_amp = 0.5;
+    p->Dn = 1.0;
+    p->theta = 1.0;
+    p->bM = 0.71;
+    p->r0sq = 6.25;
+    p->dt = 0.0;
+    p->cfl_frac = 0.2;
+    p->b_threshold = 0.0;
+    p->chemo_law = CX_CHEMO_RECEPTOR;
+    p->mobility = CX_MOBILITY_CENTRAL;
+    p->noise_dist = CX_NOISE_UNIFORM;
+    p->noise_mode = CX_NOISE_STATIC;
+    p->scheme = CX_SCHEME_EULER;
+    p->precision = CX_PREC_F32;
+    return CX_OK;
+}
+
+int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit)
+{
+    int rc = validate(g, p);
+    if (rc) return rc;
+    if (!limit) return fail(CX_ERR_INVALID_ARG, "limit must not be NULL");
+    *limit = dt_limit_of(g, p);
+    return CX_OK;
+}
+
+static int resolve_dt(const cx_grid *g, const cx_params *p, double *dt)
+{
+    const double lim = dt_limit_of(g, p);
+    if (p->dt == 0.0) {
+        *dt = p->cfl_frac * lim;
+    } else {
+        if (p->dt > lim)
+            return fail(CX_ERR_DT_UNSTABLE, "dt = %.17g exceeds the stability limit %.17g", p->dt, lim);
+        *dt = p->dt;
+    }
+    return CX_OK;
+}
+
+int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
+{
+    if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    int rc = validate(g, p);
+    if (rc) return rc;
+    if (p->noise_mode == CX_NOISE_PER_STEP || p->scheme == CX_SCHEME_HEUN)
+        return fail(CX_ERR_UNSUPPORTED, "per-step noise and the Heun scheme are not built yet");
+    double dt;
+    rc = resolve_dt(g, p, &dt);
+    if (rc) return rc;
+    cx_ctx *c;
+    rc = alloc_ctx(g, p, seed, dt, &c);
+    if (rc) return rc;
+    cudaError_t e = cx::launch_sigma_init(c->prec, c->sigma, g->nx, g->ny, c->pitch, seed, 0,
+                                          p->sigma0, p->noise_amp, p->noise_dist, c->stream);
+    if (e == cudaSuccess)
+        e = cx::launch_initial_state(c->prec, c->b[0], c->n[0], g->nx, g->ny, c->pitch, g->dx,
+                                     p->n0, p->bM, p->r0sq, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cx_destroy(c);
+        return cuda_fail(e, "initialisation kernels");
+    }
+    *out = c;
+    return CX_OK;
+}
+
+int cx_set_stream(cx_ctx *c, void *stream)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    c->stream = (cudaStream_t)stream;
+    return CX_OK;
+}
+
+int cx_step(cx_ctx *c, int64_t n_steps)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n_steps < 0) return fail(CX_ERR_INVALID_ARG, "n_steps = %lld < 0", (long long)n_steps);
+    cx::StepArgs a;
+    a.nx = c->g.nx;
+    a.ny = c->g.ny;
+    a.pitch = c->pitch;
+    a.law = c->p.chemo_law;
+    a.mob = c->p.mobility;
+    a.k = coef_of(c);
+    a.sg.per_step = 0;
+    a.sg.dist = c->p.noise_dist;
+    a.sg.sigma0 = c->p.sigma0;
+    a.sg.amp = c->p.noise_amp;
+    a.sg.seed = c->seed;
+    a.s = c->sigma;
+    for (int64_t m = 0; m < n_steps; ++m) {
+        a.b = c->b[c->cur];
+        a.n = c->n[c->cur];
+        a.bo = c->b[c->cur ^ 1];
+        a.no = c->n[c->cur ^ 1];
+        a.step = c->step;
+        cudaError_t e = cx::launch_step(c->prec, a, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    return CX_OK;
+}
+
+int cx_synchronize(cx_ctx *c)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    CX_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return CX_OK;
+}
+
+int cx_diagnostics(cx_ctx *c, cx_diag *out)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
+    const double bth = b_threshold_of(&c->p);
+    CX_CUDA(cx::launch_diagnostics(c->prec, c->b[c->cur], c->n[c->cur], c->g.nx, c->g.ny,
+                                   c->pitch, bth, c->diag, c->stream),
+            "diagnostics launch");
+    CX_CUDA(cudaMemcpyAsync(c->h_diag, c->diag.result, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream),
+            "diagnostics copy");
+    CX_CUDA(cudaStreamSynchronize(c->stream), "diagnostics synchronize");
+    const double *h = c->h_diag;
+    const double area = c->g.dx * c->g.dx;
+    memset(out, 0, sizeof *out);
+    out->step = c->step;
+    out->dt = c->dt;
+    out->t = (double)c->step * c->dt;
+    out->mass_b = area * h[0];
+    out->mass_n = area * h[1];
+    out->invariant = area * (h[0] + c->p.theta * h[1]);
+    out->min_b = h[2];
+    out->min_n = h[3];
+    out->max_b = h[4];
+    out->r_env = h[5] >= 0.0 ? 0.5 * c->g.dx * sqrt(h[5]) : 0.0;
+    out->finite = h[6] == 0.0 ? 1 : 0;
+    out->status = CX_OK;
+    if (!out->finite)
+        out->status = CX_ERR_NONFINITE;
+    else if (out->min_b < 0.0 || out->min_n < 0.0)
+        out->status = CX_ERR_NEGATIVE;
+    if (out->status != CX_OK)
+        return fail(out->status, "state at step %lld: %s", (long long)c->step,
+                    cx_strerror(out->status));
+    return CX_OK;
+}
+
+static int check_io(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size_t count)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!host) return fail(CX_ERR_INVALID_ARG, "host pointer must not be NULL");
+    if (which < CX_FIELD_B || which > CX_FIELD_SIGMA) return fail(CX_ERR_INVALID_ARG, "field %d", which);
+    if (dtype != CX_F64 && dtype != CX_F32) return fail(CX_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (count != (size_t)c->g.nx * (size_t)c->g.ny)
+        return fail(CX_ERR_INVALID_ARG, "count %zu != nx*ny = %zu", count,
+                    (size_t)c->g.nx * (size_t)c->g.ny);
+    return CX_OK;
+}
+
+int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t count)
+{
+    int rc = check_io(c, which, host, dtype, count);
+    if (rc) return rc;
+    const size_t row = (size_t)c->g.nx * c->elem;
+    const int state_dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    CX_CUDA(cudaStreamSynchronize(c->stream), "synchronize before field read");
+    if (dtype == state_dtype) {
+        CX_CUDA(cudaMemcpy2DAsync(host, row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
+                                  c->g.ny, cudaMemcpyDeviceToHost, c->stream),
+                "field copy to host");
+        CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
+        return CX_OK;
+    }
+    // precision change: copy in the state type, widen or narrow on the host
+    std::vector<unsigned char> tmp;
+    try { tmp.resize(count * c->elem); } catch (...) { return fail(CX_ERR_OOM, "host staging"); }
+    CX_CUDA(cudaMemcpy2DAsync(tmp.data(), row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
+                              c->g.ny, cudaMemcpyDeviceToHost, c->stream),
+            "field copy to host");
+    CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
+    if (state_dtype == CX_F32) {
+        const float *s = (const float *)tmp.data();
+        double *d = (double *)host;
+        for (size_t q = 0; q < count; ++q) d[q] = (double)s[q];
+    } else {
+        const double *s = (const double *)tmp.data();
+        float *d = (float *)host;
+        for (size_t q = 0; q < count; ++q) d[q] = (float)s[q];
+    }
+    return CX_OK;
+}
+
+int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size_t count)
+{
+    int rc = check_io(c, which, host, dtype, count);
+    if (rc) return rc;
+    if (which == CX_FIELD_SIGMA && c->p.noise_mode == CX_NOISE_PER_STEP)
+        return fail(CX_ERR_INVALID_ARG, "sigma is regenerated every step with per-step noise");
+    const size_t row = (size_t)c->g.nx * c->elem;
+    const int state_dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    CX_CUDA(cudaStreamSynchronize(c->stream), "synchronize before field write");
+    const void *src = host;
+    std::vector<unsigned char> tmp;
+    if (dtype != state_dtype) {
+        try { tmp.resize(count * c->elem); } catch (...) { return fail(CX_ERR_OOM, "host staging"); }
+        if (state_dtype == CX_F32) {
+            const double *s = (const double *)host;
+            float *d = (float *)tmp.data();
+            for (size_t q = 0; q < count; ++q) d[q] = (float)s[q];
+        } else {
+            const float *s = (const float *)host;
+            double *d = (double *)tmp.data();
+            for (size_t q = 0; q < count; ++q) d[q] = (double)s[q];
+        }
+        src = tmp.data();
+    }
+    CX_CUDA(cudaMemcpy2DAsync(field_ptr(c, which), (size_t)c->pitch * c->elem, src, row, row,
+                              c->g.ny, cudaMemcpyHostToDevice, c->stream),
+            "field copy to device");
+    CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
+    return CX_OK;
+}
+
+int cx_get_config(cx_ctx *c, cx_grid *g, cx_params *p, uint64_t *seed)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (g) *g = c->g;
+    if (p) {
+        *p = c->p;
+        p->dt = c->dt;
+    }
+    if (seed) *seed = c->seed;
+    return CX_OK;
+}
+
+int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (step) *step = c->step;
+    if (t) *t = (double)c->step * c->dt;
+    if (dt) *dt = c->dt;
+    return CX_OK;
+}
+
+int cx_set_step(cx_ctx *c, int64_t step)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (step < 0) return fail(CX_ERR_INVALID_ARG, "step = %lld < 0", (long long)step);
+    c->step = step;
+    return CX_OK;
+}
+
+int cx_set_time_block(cx_ctx *c, int32_t k)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (k < 1 || k > 8) return fail(CX_ERR_INVALID_ARG, "time block %d outside 1..8", k);
+    c->time_block = k;
+    return CX_OK;
+}
+
+int cx_get_time_block(cx_ctx *c, int32_t *k)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!k) return fail(CX_ERR_INVALID_ARG, "k must not be NULL");
+    *k = c->time_block;
+    return CX_OK;
+}
+
+// Checkpoint layout (little-endian host order):
+//   char magic[8] = "CXCKPT01"; cx_grid; cx_params; uint64 seed; int64 step;
+//   double dt; int32 precision; int32 reserved;
+//   then b, n, sigma as nx*ny elements each in the state precision.
+static const char kMagic[8] = {'C', 'X', 'C', 'K', 'P', 'T', '0', '1'};
+
+int cx_save(cx_ctx *c, const char *path)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!path) return fail(CX_ERR_INVALID_ARG, "path must not be NULL");
+    const size_t count = (size_t)c->g.nx * (size_t)c->g.ny;
+    std::vector<unsigned char> buf;
+    try { buf.resize(count * c->elem); } catch (...) { return fail(CX_ERR_OOM, "host staging"); }
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(CX_ERR_IO, "cannot open %s for writing", path);
+    const int32_t prec = c->prec, reserved = 0;
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&c->g, sizeof c->g, 1, f) == 1 &&
+              fwrite(&c->p, sizeof c->p, 1, f) == 1 && fwrite(&c->seed, 8, 1, f) == 1 &&
+              fwrite(&c->step, 8, 1, f) == 1 && fwrite(&c->dt, 8, 1, f) == 1 &&
+              fwrite(&prec, 4, 1, f) == 1 && fwrite(&reserved, 4, 1, f) == 1;
+    const int dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    for (int w = CX_FIELD_B; ok && w <= CX_FIELD_SIGMA; ++w) {
+        rc = cx_get_field(c, w, buf.data(), dtype, count);
+        if (rc) { fclose(f); return rc; }
+        ok = fwrite(buf.data(), c->elem, count, f) == count;
+    }
+    if (fclose(f) != 0) ok = false;
+    if (!ok) return fail(CX_ERR_IO, "short write to %s", path);
+    return CX_OK;
+}
+
+int cx_load(const char *path, cx_ctx **out)
+{
+    if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (!path) return fail(CX_ERR_INVALID_ARG, "path must not be NULL");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(CX_ERR_IO, "cannot open %s", path);
+    char magic[8];
+    cx_grid g;
+    cx_params p;
+    uint64_t seed;
+    int64_t step;
+    double dt;
+    int32_t prec, reserved;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+              fread(&g, sizeof g, 1, f) == 1 && fread(&p, sizeof p, 1, f) == 1 &&
+              fread(&seed, 8, 1, f) == 1 && fread(&step, 8, 1, f) == 1 &&
+              fread(&dt, 8, 1, f) == 1 && fread(&prec, 4, 1, f) == 1 &&
+              fread(&reserved, 4, 1, f) == 1;
+    if (!ok || prec != p.precision) {
+        fclose(f);
+        return fail(CX_ERR_IO, "%s is not a checkpoint of this library", path);
+    }
+    int rc = validate(&g, &p);
+    if (rc) { fclose(f); return rc; }
+    if (!(isfinite(dt) && dt > 0.0) || step < 0) {
+        fclose(f);
+        return fail(CX_ERR_IO, "%s: bad time step or step count", path);
+    }
+    cx_ctx *c;
+    rc = alloc_ctx(&g, &p, seed, dt, &c);
+    if (rc) { fclose(f); return rc; }
+    c->step = step;
+    const size_t count = (size_t)g.nx * (size_t)g.ny;
+    std::vector<unsigned char> buf;
+    try { buf.resize(count * c->elem); } catch (...) { fclose(f); cx_destroy(c); return fail(CX_ERR_OOM, "host staging"); }
+    const int dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    for (int w = CX_FIELD_B; w <= CX_FIELD_SIGMA; ++w) {
+        if (fread(buf.data(), c->elem, count, f) != count) {
+            fclose(f);
+            cx_destroy(c);
+            return fail(CX_ERR_IO, "%s is truncated", path);
+        }
+        // sigma is written even for per-step noise (it is then regenerated)
+        if (w == CX_FIELD_SIGMA && p.noise_mode == CX_NOISE_PER_STEP) continue;
+        rc = cx_set_field(c, w, buf.data(), dtype, count);
+        if (rc) { fclose(f); cx_destroy(c); return rc; }
+    }
+    fclose(f);
+    *out = c;
+    return CX_OK;
+}
+
+void cx_destroy(cx_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// cx_init.cu -- sigma field and initial state.
+//
+// sigma = sigma0 (1 + a Delta) (Eq. CoefCrsDif) with Delta drawn per cell
+// from Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11), counter (cell index lo, hi, time
+// step lo, hi), key (seed lo, hi).  Delta is formed exactly in integers and
+// the products are rounded one at a time (no fused multiply-add), so the
+// field is bit-identical to any other IEEE implementation of the same
+// definition.
+//
+// Initial state (Eq. inicond, Eq. inibacexp): n = n0, b = bM exp(-r^2/r0sq)
+// with r the distance of the cell centre from the domain centre.
+#include "cx_internal.h"
+#include "cx_philox.cuh"
+
+namespace cx {
+namespace {
+
+template <typename T>
+__global__ void sigma_init_kernel(T *__restrict__ sigma, int nx, int ny, long long pitch,
+                                  uint64_t seed, uint64_t step, double sigma0, double amp,
+                                  int dist)
+{
+    const long long total = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+        const double d = noise_delta(seed, (uint64_t)c, step, dist);
+        const double s = __dmul_rn(sigma0, __dadd_rn(1.0, __dmul_rn(amp, d)));
+        sigma[(long long)j * pitch + i] = (T)s;
+    }
+}
+
+template <typename T>
+__global__ void initial_state_kernel(T *__restrict__ b, T *__restrict__ n, int nx, int ny,
+                                     long long pitch, double dx, double n0, double bM,
+                                     double r0sq)
+{
+    const long long total = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+        // (i + 1/2 - nx/2) is a half-integer: exact in FP64
+        const double x = __dmul_rn((double)i + 0.5 - 0.5 * (double)nx, dx);
+        const double y = __dmul_rn((double)j + 0.5 - 0.5 * (double)ny, dx);
+        const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+        const double e = exp(__ddiv_rn(-r2, r0sq));
+        b[(long long)j * pitch + i] = (T)__dmul_rn(bM, e);
+        n[(long long)j * pitch + i] = (T)n0;
+    }
+}
+
+int grid_for(long long total, int threads)
+{
+    long long g = (total + threads - 1) / threads;
+    return (int)(g < 152LL * 32 ? (g < 1 ? 1 : g) : 152LL * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long pitch,
+                              uint64_t seed, uint64_t step, double sigma0, double amp,
+                              int dist, cudaStream_t st)
+{
+    const int threads = 256;
+    const int grid = grid_for((long long)nx * ny, threads);
+    if (prec == CX_PREC_F64)
+        sigma_init_kernel<double><<<grid, threads, 0, st>>>((double *)sigma, nx, ny, pitch, seed,
+                                                            step, sigma0, amp, dist);
+    else
+        sigma_init_kernel<float><<<grid, threads, 0, st>>>((float *)sigma, nx, ny, pitch, seed,
+                                                           step, sigma0, amp, dist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_initial_state(int prec, void *b, void *n, int nx, int ny, long long pitch,
+                                 double dx, double n0, double bM, double r0sq, cudaStream_t st)
+{
+    const int threads = 256;
+    const int grid = grid_for((long long)nx * ny, threads);
+    if (prec == CX_PREC_F64)
+        initial_state_kernel<double><<<grid, threads, 0, st>>>((double *)b, (double *)n, nx, ny,
+                                                               pitch, dx, n0, bM, r0sq);
+    else
+        initial_state_kernel<float><<<grid, threads, 0, st>>>((float *)b, (float *)n, nx, ny,
+                                                              pitch, dx, n0, bM, r0sq);
+    return cudaGetLastError();
+}
+
+}  // namespace cx

@@ -1,0 +1,87 @@
+// cx_internal.h -- internal declarations shared by the library's translation
+// units: the handle layout, kernel argument blocks and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cx.h"
+
+namespace cx {
+
+// Per-run coefficients of the scaled face fluxes.  The kernels work with
+// fluxes pre-multiplied by dt/dx, so that one step reads
+//   b' = b + (phiE - phiW + phiN - phiS) + dt theta n b
+//   n' = n + (gE - gW + gN - gS)         - dt n b
+// with, on a face between L (left/lower) and R (right/upper),
+//   hc  = chi(n_f) / 2 = cChi / (2+n2)^2 (receptor law) or cChi (constant law)
+//   phi = cA s2 n2 b2 (db - hc b2 dn)                   central mobility b_f^2
+//   phi = cA s2 n2 (b2 db - 4 hc b_d^2 dn)              donor-cell mobility b_d^2
+//   g   = cG dn
+// where s2 = sL+sR, n2 = nL+nR, b2 = bL+bR, db = bR-bL, dn = nR-nL and b_d
+// is b of the lower-n cell.  Derivation: sigma_f n_f b_f = s2 n2 b2 / 8,
+// b_f^2 = b2^2 / 4 and, for the receptor law, chi(n_f) = 4 chi0 / (2+n2)^2.
+struct Coef {
+    double cA;    // dt / (8 dx^2)
+    double cChi;  // receptor: 2 chi0; constant: chi0 / 2
+    double cG;    // dt Dn / dx^2
+    double cR;    // dt theta
+    double cN;    // dt
+};
+
+struct Sigma {  // how sigma is obtained
+    int per_step;     // 0: read the sigma array; 1: regenerate from Philox
+    int dist;         // CX_NOISE_*
+    double sigma0, amp;
+    uint64_t seed;
+};
+
+struct StepArgs {
+    const void *b, *n, *s;  // current state (+ sigma array, static noise)
+    void *bo, *no;          // next state
+    int nx, ny;
+    long long pitch;        // elements per row
+    int law, mob;
+    Coef k;
+    Sigma sg;
+    long long step;         // index of the time step being taken
+};
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long pitch,
+                              uint64_t seed, uint64_t step, double sigma0, double amp,
+                              int dist, cudaStream_t st);
+cudaError_t launch_initial_state(int prec, void *b, void *n, int nx, int ny, long long pitch,
+                                 double dx, double n0, double bM, double r0sq, cudaStream_t st);
+cudaError_t launch_step(int prec, const StepArgs &a, cudaStream_t st);
+
+struct DiagScratch {
+    double *partials;  // [blocks][8]
+    double *result;    // [8] on the device
+    int blocks;
+};
+int diag_blocks_for(int ny);
+cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, int ny,
+                               long long pitch, double b_threshold, DiagScratch s,
+                               cudaStream_t st);
+
+}  // namespace cx
+
+struct cx_ctx {
+    cx_grid g;
+    cx_params p;
+    uint64_t seed;
+    int prec;             // CX_PREC_*
+    size_t elem;          // bytes per element
+    long long pitch;      // elements per row (rows 128-byte aligned)
+    void *b[2], *n[2];    // ping-pong state
+    void *sigma;
+    int cur;              // index of the buffer holding the current state
+    int64_t step;
+    double dt;
+    cudaStream_t stream;
+    int device;
+    int time_block;
+    cx::DiagScratch diag;
+    double *h_diag;       // pinned [8]
+};

@@ -1,0 +1,49 @@
+// cx_philox.cuh -- Philox4x32-10 counter-based generator (Salmon, Moraes,
+// Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) and
+// the random perturbation Delta of the motility sigma (Eq. CoefCrsDif;
+// Sec. 3 draws it "on every grid point and at each time step" from a
+// triangular law on [-1,1]).
+#pragma once
+
+#include <stdint.h>
+
+namespace cx {
+
+// One Philox4x32 block, 10 rounds.  A round maps (c0,c1,c2,c3) to
+//   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// and the key advances by the Weyl increments (W0, W1) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+// Delta of cell `idx` at time step `step`.  Two 53-bit integers are cut
+// from the output words, k_a = (w0 << 21) | (w1 >> 11), k_b likewise from
+// (w2, w3); U = k 2^-53 is uniform on [0,1).
+//   dist 0:  Delta = 2 U_a - 1          uniform on [-1,1)
+//   dist 1:  Delta = U_a + U_b - 1      triangular on (-1,1)
+// The numerator is an exact integer below 2^53 in magnitude, so the
+// conversion and the power-of-two scaling are exact.
+__device__ __forceinline__ double noise_delta(uint64_t seed, uint64_t idx, uint64_t step, int dist)
+{
+    const uint4 w = philox4x32_10(
+        make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
+        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const long long ka = (long long)(((unsigned long long)w.x << 21) | (unsigned long long)(w.y >> 11));
+    const long long kb = (long long)(((unsigned long long)w.z << 21) | (unsigned long long)(w.w >> 11));
+    const long long two53 = 1LL << 53;
+    const long long num = dist == 0 ? 2 * ka - two53 : ka + kb - two53;
+    return (double)num * 0x1p-53;
+}
+
+}  // namespace cx
