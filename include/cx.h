@@ -209,6 +209,52 @@ int cx_load(const char *path, cx_ctx **out);
 /* Free the handle and its device buffers.  NULL is a no-op. */
 void cx_destroy(cx_ctx *c);
 
+/* ---- diagnostics without any allocation --------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device or pinned memory themselves.  Examples: a framework
+ * whose caching allocator owns all device memory (a stray cudaMalloc or
+ * cudaFree synchronises the whole device and fragments that pool), a
+ * service that sized its device memory once at start-up and must stay
+ * within that budget, or a time-critical loop in which a blocking
+ * allocation is not allowed.
+ *
+ * It computes the same reduction as cx_diagnostics, with the same kernels
+ * and the same summation order, over fields the caller owns:
+ *   b, n        device arrays of nx*ny cells, row j at element j*pitch,
+ *               FP64 or FP32 as `precision` (CX_PREC_*) says;
+ *   pitch       elements per row, >= nx;
+ *   dx, theta   cell size (> 0) and conversion factor (>= 0) for the
+ *               masses and the invariant dx^2 sum (b + theta n);
+ *   b_threshold envelope level for r_env (> 0);
+ *   stream      cudaStream_t to run on (NULL = legacy default stream);
+ *   result_dev  caller-owned device array of 8 doubles that receives
+ *               {sum b, sum n, min b, min n, max b, max (2i+1-nx)^2 +
+ *               (2j+1-ny)^2 over b >= b_threshold (-1 if none),
+ *               non-finite flag, 0};
+ *   out         optional host struct: if non-NULL the call copies the
+ *               record back, waits for `stream` and fills *out (step, t and
+ *               dt are 0: there is no handle).  If NULL the call only
+ *               queues work on `stream` and returns.
+ * The per-block partial records live in one static device array of 1024
+ * records x 8 doubles (64 KiB), which every GPU that loads the library holds
+ * until the process exits.  The reduction uses at most 1024 blocks for any
+ * grid, so every grid within the library's limits fits: nx, ny >= 1,
+ * nx*ny <= 2^32 and ny <= 2,097,120; larger sizes are rejected with
+ * CX_ERR_INVALID_ARG.  The call allocates nothing and frees nothing.
+ *
+ * All calls share that one array and it keeps the last call's contents;
+ * every record a call reads is written earlier in the same call, so nothing
+ * needs clearing.  Calls that overlap on the GPU (on different streams, or
+ * from different threads) race on the array and must be serialised by the
+ * caller.  The first call on each device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  Errors: INVALID_ARG, CUDA, and NONFINITE / NEGATIVE
+ * (with *out filled) as for cx_diagnostics when `out` is given. */
+int cx_diagnostics_noalloc(const void *b, const void *n, int32_t nx, int32_t ny, int64_t pitch,
+                           int32_t precision, double dx, double theta, double b_threshold,
+                           void *stream, double *result_dev, cx_diag *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,10 @@ _SIGNATURES = {
     "cx_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "cx_destroy": (None, [_P]),
+    "cx_diagnostics_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, _P, _P,
+                                              ctypes.POINTER(cx_diag)]),
 }
 
 _lib = None
@@ -240,6 +244,20 @@ def cx_load(path: str) -> int:
 def cx_destroy(h):
     if h:
         lib().cx_destroy(h)
+
+
+def cx_diagnostics_noalloc(b_ptr, n_ptr, nx, ny, pitch, precision, dx, theta, b_threshold,
+                           stream, result_ptr, want_host=True):
+    """Diagnostics over caller-owned device fields (raw device pointers),
+    with no allocation by the library; returns a cx_diag when want_host,
+    else None after queueing the work on `stream`."""
+    d = cx_diag() if want_host else None
+    rc = lib().cx_diagnostics_noalloc(b_ptr, n_ptr, nx, ny, pitch, precision, dx, theta,
+                                      b_threshold, stream, result_ptr,
+                                      ctypes.byref(d) if want_host else None)
+    if rc not in (CX_OK, CX_ERR_NONFINITE, CX_ERR_NEGATIVE) or not want_host:
+        _check(rc)
+    return d
 
 
 # ---- convenience wrapper -----------------------------------------------------

@@ -185,6 +185,8 @@ void *field_ptr(cx_ctx *c, int which)
 
 }  // namespace
 
+int cx::record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 int cx_version(void) { return CX_VERSION; }

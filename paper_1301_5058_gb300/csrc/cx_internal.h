@@ -65,6 +65,9 @@ cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, i
                                long long pitch, double b_threshold, DiagScratch s,
                                cudaStream_t st);
 
+// Store `msg` as this thread's cx_last_error() text; returns `code`.
+int record_error(int code, const char *msg);
+
 }  // namespace cx
 
 struct cx_ctx {
