@@ -30,7 +30,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"f32": 20, "f64": 40}  # read b, n, sigma; write b', n'
+# algorithmic HBM bytes per cell and time step: Euler reads b, n (and the
+# sigma array for static noise) and writes b', n'; Heun's second stage also
+# reads the start-of-step state pointwise
+def bytes_per_cell(prec, scheme, noise):
+    w = 4 if prec == "f32" else 8
+    euler = (5 if noise == "static" else 4) * w
+    return euler if scheme == "euler" else euler + euler + 2 * w
 
 
 def parse():
@@ -43,6 +49,9 @@ def parse():
     ap.add_argument("--n", type=int, default=16384, help="grid side")
     ap.add_argument("--chi0", type=float, default=1.0)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--scheme", default="euler", choices=["euler", "heun"])
+    ap.add_argument("--noise", default="static", choices=["static", "per-step"])
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "triangular"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -57,7 +66,8 @@ def workload(args):
 def config_block(args, cfg):
     return {"workload": f"single grid {cfg['nx']}x{cfg['ny']} {args.precision} state, "
                         f"n0={cfg['n0']} sigma0={cfg['sigma0']} a={cfg['noise_amp']} "
-                        f"chi0={cfg['chi0']} receptor law, static uniform noise, forward Euler, "
+                        f"chi0={cfg['chi0']} receptor law, {args.noise} {args.dist} noise, "
+                        f"{'forward Euler' if args.scheme == 'euler' else 'Heun RK2'}, "
                         f"dt=0.2 x limit",
             "nx": cfg["nx"], "ny": cfg["ny"], "time_steps_per_step": args.window,
             "diagnostics_per_step": 1,
@@ -160,6 +170,9 @@ def run_ours(args, rank, world, local_rank):
     cfg = workload(args)
     grid, params, seed = W.split(cfg)
     params["precision"] = cx.CX_PREC_F32 if args.precision == "f32" else cx.CX_PREC_F64
+    params["scheme"] = cx.CX_SCHEME_EULER if args.scheme == "euler" else cx.CX_SCHEME_HEUN
+    params["noise_mode"] = cx.CX_NOISE_STATIC if args.noise == "static" else cx.CX_NOISE_PER_STEP
+    params["noise_dist"] = cx.CX_NOISE_UNIFORM if args.dist == "uniform" else cx.CX_NOISE_TRIANGULAR
     seed = seed + rank
     sim = cx.Sim(grid["nx"], grid["ny"], grid["dx"], seed=seed, **params)
     stream = torch.cuda.current_stream(dev)
@@ -295,7 +308,8 @@ def main():
     units = cells * S * K * world
     value = units / elapsed
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_CELL[args.precision] * cells / per_launch / 1e9
+    bpc = bytes_per_cell(args.precision, args.scheme, args.noise)
+    achieved = bpc * cells / per_launch / 1e9
     out = {
         "metric": "grid-cell updates/s",
         "value": value,
@@ -313,9 +327,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": step_kernel_traffic(args.precision),
-                     "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision],
-                     "kernel_ms_per_launch": per_launch * 1e3},
-        "gpu_launches": K * (S + 2),
+                     "algorithmic_bytes_per_cell": bpc,
+                     "kernel_ms_per_time_step": per_launch * 1e3,
+                     "launches_per_time_step": 1 if args.scheme == "euler" else 2},
+        "gpu_launches": K * (S * (1 if args.scheme == "euler" else 2) + 2),
         "clocks": r["clocks"],
         "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b", "min_n")},
     }

@@ -61,6 +61,8 @@ def _load():
     lib.orc_noise_delta.restype = _D
     lib.orc_sigma_field.argtypes = [_I, _I, _U64, _U64, _D, _D, _I, _PD]
     lib.orc_sigma_field.restype = None
+    lib.orc_sigma_field_f32.argtypes = [_I, _I, _U64, _U64, _D, _D, _I, _PD]
+    lib.orc_sigma_field_f32.restype = None
     lib.orc_initial_state.argtypes = [_I, _I, _D, _D, _D, _D, _PD, _PD]
     lib.orc_initial_state.restype = None
     lib.orc_rhs.argtypes = [_I, _I, _D, _D, _D, _D, _I, _I, _PD, _PD, _PD, _PD, _PD]
@@ -69,7 +71,7 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = [_I, _I, _D, _D, _D, _D, _D, _I, _I, _PD, _PD, _PD, _PD, _PD]
         f.restype = _I
-    lib.orc_run.argtypes = [_I, _I, _D, _D, _D, _D, _D, _I, _I, _I, _I, _U64, _D, _D, _I,
+    lib.orc_run.argtypes = [_I, _I, _D, _D, _D, _D, _D, _I, _I, _I, _I, _I, _U64, _D, _D, _I,
                             _I64, _I64, _PD, _PD, _PD]
     lib.orc_run.restype = _I
     lib.orc_diagnostics.argtypes = [_I, _I, _D, _D, _D, _PD, _PD, _PD]
@@ -112,6 +114,15 @@ def sigma_field(nx, ny, seed, sigma0, amp, dist=0, step=0) -> np.ndarray:
     return s
 
 
+def sigma_field_f32(nx, ny, seed, sigma0, amp, dist=0, step=0) -> np.ndarray:
+    """The FP32 recipe of the same draw (24-bit uniforms, float arithmetic),
+    used by FP32-state runs whose sigma is redrawn every step; returned as
+    float64 (exactly the float values)."""
+    s = np.empty((ny, nx), np.float64)
+    _load().orc_sigma_field_f32(nx, ny, seed, step, sigma0, amp, dist, _ptr(s))
+    return s
+
+
 def initial_state(nx, ny, dx, n0, bM, r0sq):
     """n = n0, b = bM exp(-r^2/r0sq) (Eq. inicond, Eq. inibacexp)."""
     b = np.empty((ny, nx), np.float64)
@@ -147,15 +158,16 @@ def step(sigma, b, n, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0, schem
 
 
 def run(sigma, b, n, nsteps, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0,
-        scheme=0, noise_mode=0, seed=0, sigma0=0.0, amp=0.0, dist=0, step0=0):
+        scheme=0, noise_mode=0, seed=0, sigma0=0.0, amp=0.0, dist=0, step0=0, recipe=0):
     """Advance (b, n) by `nsteps` steps in place (copies are returned).  With
-    noise_mode 1 sigma is redrawn from (seed, cell, m) before every step m."""
+    noise_mode 1 sigma is redrawn from (seed, cell, m) before every step m,
+    by the FP64 recipe (recipe 0) or the FP32 recipe (recipe 1)."""
     s = np.array(sigma, np.float64, order="C", copy=True)
     bb = np.array(b, np.float64, order="C", copy=True)
     nn = np.array(n, np.float64, order="C", copy=True)
     ny, nx = bb.shape
     rc = _load().orc_run(nx, ny, dx, dt, Dn, theta, chi0, chemo_law, mobility, scheme,
-                         noise_mode, seed, sigma0, amp, dist, step0, nsteps,
+                         noise_mode, recipe, seed, sigma0, amp, dist, step0, nsteps,
                          _ptr(s), _ptr(bb), _ptr(nn))
     if rc != 0:
         raise MemoryError("oracle run: allocation failed")

@@ -94,6 +94,38 @@ double orc_noise_delta(uint64_t seed, uint64_t idx, uint64_t step, int dist)
     return ldexp((double)num, -53);
 }
 
+/* FP32 recipe of the same draw, used when the state is held in FP32 and
+ * sigma is redrawn every step: 24-bit integers j_a = w0 >> 8, j_b = w2 >> 8,
+ *   dist 0:  Delta = (2 j_a - 2^24) 2^-24,   dist 1:  Delta = (j_a + j_b - 2^24) 2^-24,
+ * exact in float, then sigma = sigma0 (1 + a Delta) with each float
+ * operation rounded on its own. */
+float orc_noise_sigma_f32(uint64_t seed, uint64_t idx, uint64_t step, int dist,
+                          float sigma0, float amp)
+{
+    uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32),
+                       (uint32_t)step, (uint32_t)(step >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    int32_t ja = (int32_t)(w[0] >> 8), jb = (int32_t)(w[2] >> 8);
+    int32_t num = (dist == 0) ? (2 * ja - (1 << 24)) : (ja + jb - (1 << 24));
+    float d = (float)num * 0x1p-24f;
+    float t = amp * d;
+    float s = 1.0f + t;
+    return sigma0 * s;
+}
+
+void orc_sigma_field_f32(int nx, int ny, uint64_t seed, uint64_t step, double sigma0,
+                         double amp, int dist, double *sigma)
+{
+    float s0 = (float)sigma0, a = (float)amp;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            uint64_t idx = (uint64_t)j * (uint64_t)nx + (uint64_t)i;
+            sigma[idx] = (double)orc_noise_sigma_f32(seed, idx, step, dist, s0, a);
+        }
+}
+
 /* sigma_ij = sigma0 (1 + a Delta_ij)   (Eq. CoefCrsDif) */
 void orc_sigma_field(int nx, int ny, uint64_t seed, uint64_t step,
                      double sigma0, double amp, int dist, double *sigma)
@@ -256,10 +288,11 @@ int orc_step_heun(int nx, int ny, double dx, double dt, double Dn,
 /* Run `nsteps` steps in place starting at time-step index `step0`.
  * scheme 0 Euler, 1 Heun.  noise_mode 0: `sigma` is a fixed field and is
  * used as given; noise_mode 1: sigma is redrawn before every step m from
- * (seed, cell, m) with sigma0, amp, dist and written into `sigma`. */
+ * (seed, cell, m) with sigma0, amp, dist and written into `sigma`, by the
+ * FP64 recipe (recipe 0) or the FP32 recipe (recipe 1). */
 int orc_run(int nx, int ny, double dx, double dt, double Dn, double theta,
             double chi0, int chemo_law, int mobility, int scheme,
-            int noise_mode, uint64_t seed, double sigma0, double amp, int dist,
+            int noise_mode, int recipe, uint64_t seed, double sigma0, double amp, int dist,
             int64_t step0, int64_t nsteps, double *sigma, double *b, double *n)
 {
     size_t N = (size_t)nx * (size_t)ny;
@@ -268,8 +301,10 @@ int orc_run(int nx, int ny, double dx, double dt, double Dn, double theta,
     if (!b2 || !n2) { free(b2); free(n2); return -1; }
     int rc = 0;
     for (int64_t m = 0; m < nsteps && rc == 0; ++m) {
-        if (noise_mode == 1)
+        if (noise_mode == 1 && recipe == 0)
             orc_sigma_field(nx, ny, seed, (uint64_t)(step0 + m), sigma0, amp, dist, sigma);
+        else if (noise_mode == 1)
+            orc_sigma_field_f32(nx, ny, seed, (uint64_t)(step0 + m), sigma0, amp, dist, sigma);
         if (scheme == 0)
             rc = orc_step_euler(nx, ny, dx, dt, Dn, theta, chi0, chemo_law, mobility,
                                 sigma, b, n, b2, n2);

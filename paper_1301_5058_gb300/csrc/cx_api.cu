@@ -183,6 +183,22 @@ void *field_ptr(cx_ctx *c, int which)
     return c->sigma;
 }
 
+// Which sigma recipe the handle uses: per-step noise of an FP32 state uses
+// the FP32 recipe, everything else the FP64 one.
+int sigma_recipe(const cx_ctx *c)
+{
+    return (c->p.noise_mode == CX_NOISE_PER_STEP && c->prec == CX_PREC_F32) ? 1 : 0;
+}
+
+// Write into the sigma array the field of time step `step` (per-step noise)
+// or the static field (step 0).
+cudaError_t fill_sigma(cx_ctx *c, int64_t step)
+{
+    return cx::launch_sigma_init(c->prec, c->sigma, c->g.nx, c->g.ny, c->pitch, c->seed,
+                                 (uint64_t)step, c->p.sigma0, c->p.noise_amp, c->p.noise_dist,
+                                 sigma_recipe(c), c->stream);
+}
+
 }  // namespace
 
 int cx::record_error(int code, const char *msg) { return fail(code, "%s", msg); }
@@ -262,16 +278,13 @@ int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
     *out = nullptr;
     int rc = validate(g, p);
     if (rc) return rc;
-    if (p->noise_mode == CX_NOISE_PER_STEP || p->scheme == CX_SCHEME_HEUN)
-        return fail(CX_ERR_UNSUPPORTED, "per-step noise and the Heun scheme are not built yet");
     double dt;
     rc = resolve_dt(g, p, &dt);
     if (rc) return rc;
     cx_ctx *c;
     rc = alloc_ctx(g, p, seed, dt, &c);
     if (rc) return rc;
-    cudaError_t e = cx::launch_sigma_init(c->prec, c->sigma, g->nx, g->ny, c->pitch, seed, 0,
-                                          p->sigma0, p->noise_amp, p->noise_dist, c->stream);
+    cudaError_t e = fill_sigma(c, 0);
     if (e == cudaSuccess)
         e = cx::launch_initial_state(c->prec, c->b[0], c->n[0], g->nx, g->ny, c->pitch, g->dx,
                                      p->n0, p->bM, p->r0sq, c->stream);
@@ -304,21 +317,38 @@ int cx_step(cx_ctx *c, int64_t n_steps)
     a.law = c->p.chemo_law;
     a.mob = c->p.mobility;
     a.k = coef_of(c);
-    a.sg.per_step = 0;
+    a.sg.per_step = c->p.noise_mode == CX_NOISE_PER_STEP;
     a.sg.dist = c->p.noise_dist;
     a.sg.sigma0 = c->p.sigma0;
     a.sg.amp = c->p.noise_amp;
     a.sg.seed = c->seed;
     a.s = c->sigma;
+    const bool heun = c->p.scheme == CX_SCHEME_HEUN;
     for (int64_t m = 0; m < n_steps; ++m) {
+        // Euler step, or Heun's first stage u* = u + dt r(u), into the other buffer
         a.b = c->b[c->cur];
         a.n = c->n[c->cur];
+        a.bu = a.nu = nullptr;
         a.bo = c->b[c->cur ^ 1];
         a.no = c->n[c->cur ^ 1];
+        a.stage = 0;
         a.step = c->step;
         cudaError_t e = cx::launch_step(c->prec, a, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        c->cur ^= 1;
+        if (heun) {
+            // second stage: u' = (u + u* + dt r(u*)) / 2, written over u
+            a.b = c->b[c->cur ^ 1];
+            a.n = c->n[c->cur ^ 1];
+            a.bu = c->b[c->cur];
+            a.nu = c->n[c->cur];
+            a.bo = c->b[c->cur];
+            a.no = c->n[c->cur];
+            a.stage = 1;
+            e = cx::launch_step(c->prec, a, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "Heun stage launch");
+        } else {
+            c->cur ^= 1;
+        }
         c->step += 1;
     }
     return CX_OK;
@@ -389,6 +419,9 @@ int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t cou
     if (rc) return rc;
     const size_t row = (size_t)c->g.nx * c->elem;
     const int state_dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    // with per-step noise, sigma is the field the next step will use
+    if (which == CX_FIELD_SIGMA && c->p.noise_mode == CX_NOISE_PER_STEP)
+        CX_CUDA(fill_sigma(c, c->step), "sigma regeneration");
     CX_CUDA(cudaStreamSynchronize(c->stream), "synchronize before field read");
     if (dtype == state_dtype) {
         CX_CUDA(cudaMemcpy2DAsync(host, row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,

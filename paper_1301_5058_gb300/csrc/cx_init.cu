@@ -6,7 +6,9 @@
 // step lo, hi), key (seed lo, hi).  Delta is formed exactly in integers and
 // the products are rounded one at a time (no fused multiply-add), so the
 // field is bit-identical to any other IEEE implementation of the same
-// definition.
+// definition.  Two recipes exist (cx_philox.cuh): the FP64 one (static
+// noise in either precision, and per-step noise of an FP64 state) and the
+// FP32 one (per-step noise of an FP32 state).
 //
 // Initial state (Eq. inicond, Eq. inibacexp): n = n0, b = bM exp(-r^2/r0sq)
 // with r the distance of the cell centre from the domain centre.
@@ -19,15 +21,19 @@ namespace {
 template <typename T>
 __global__ void sigma_init_kernel(T *__restrict__ sigma, int nx, int ny, long long pitch,
                                   uint64_t seed, uint64_t step, double sigma0, double amp,
-                                  int dist)
+                                  int dist, int recipe)
 {
     const long long total = (long long)nx * ny;
+    const float s0f = (float)sigma0, af = (float)amp;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
          c += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-        const double d = noise_delta(seed, (uint64_t)c, step, dist);
-        const double s = __dmul_rn(sigma0, __dadd_rn(1.0, __dmul_rn(amp, d)));
-        sigma[(long long)j * pitch + i] = (T)s;
+        T v;
+        if (recipe == 0)
+            v = (T)sigma_f64(seed, (uint64_t)c, step, dist, sigma0, amp);
+        else
+            v = (T)sigma_f32(seed, (uint64_t)c, step, dist, s0f, af);
+        sigma[(long long)j * pitch + i] = v;
     }
 }
 
@@ -44,7 +50,10 @@ __global__ void initial_state_kernel(T *__restrict__ b, T *__restrict__ n, int n
         const double x = __dmul_rn((double)i + 0.5 - 0.5 * (double)nx, dx);
         const double y = __dmul_rn((double)j + 0.5 - 0.5 * (double)ny, dx);
         const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-        const double e = exp(__ddiv_rn(-r2, r0sq));
+        const double q = __ddiv_rn(-r2, r0sq);
+        // exp(q) is exactly 0 in FP64 below about -745.13; skipping the call
+        // there changes no value and spares most cells of a large grid
+        const double e = q < -800.0 ? 0.0 : exp(q);
         b[(long long)j * pitch + i] = (T)__dmul_rn(bM, e);
         n[(long long)j * pitch + i] = (T)n0;
     }
@@ -60,16 +69,16 @@ int grid_for(long long total, int threads)
 
 cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long pitch,
                               uint64_t seed, uint64_t step, double sigma0, double amp,
-                              int dist, cudaStream_t st)
+                              int dist, int recipe, cudaStream_t st)
 {
     const int threads = 256;
     const int grid = grid_for((long long)nx * ny, threads);
     if (prec == CX_PREC_F64)
         sigma_init_kernel<double><<<grid, threads, 0, st>>>((double *)sigma, nx, ny, pitch, seed,
-                                                            step, sigma0, amp, dist);
+                                                            step, sigma0, amp, dist, recipe);
     else
         sigma_init_kernel<float><<<grid, threads, 0, st>>>((float *)sigma, nx, ny, pitch, seed,
-                                                           step, sigma0, amp, dist);
+                                                           step, sigma0, amp, dist, recipe);
     return cudaGetLastError();
 }
 

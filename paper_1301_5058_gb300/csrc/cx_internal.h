@@ -30,27 +30,33 @@ struct Coef {
 };
 
 struct Sigma {  // how sigma is obtained
-    int per_step;     // 0: read the sigma array; 1: regenerate from Philox
+    int per_step;     // 0: read the sigma array; 1: regenerate from Philox every step
     int dist;         // CX_NOISE_*
     double sigma0, amp;
     uint64_t seed;
 };
 
+// One launch of the step kernel.  stage 0: u_out = u + dt r(u) (forward
+// Euler, or the first Heun stage); stage 1: the second Heun stage,
+// u_out = (u0 + u + dt r(u)) / 2 with u0 read pointwise from (bu, nu) and
+// written back in place (bo == bu, no == nu).
 struct StepArgs {
-    const void *b, *n, *s;  // current state (+ sigma array, static noise)
-    void *bo, *no;          // next state
+    const void *b, *n, *s;  // stencil input state (+ sigma array, static noise)
+    const void *bu, *nu;    // stage 1: state at the start of the step
+    void *bo, *no;          // output state
     int nx, ny;
     long long pitch;        // elements per row
-    int law, mob;
+    int law, mob, stage;
     Coef k;
     Sigma sg;
-    long long step;         // index of the time step being taken
+    long long step;         // index of the time step being taken (noise counter)
 };
 
-// Launchers (return a cudaError_t from the launch).
+// Launchers (return a cudaError_t from the launch).  recipe 0: FP64 sigma
+// recipe, 1: FP32 recipe (per-step noise of an FP32 state).
 cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long pitch,
                               uint64_t seed, uint64_t step, double sigma0, double amp,
-                              int dist, cudaStream_t st);
+                              int dist, int recipe, cudaStream_t st);
 cudaError_t launch_initial_state(int prec, void *b, void *n, int nx, int ny, long long pitch,
                                  double dx, double n0, double bM, double r0sq, cudaStream_t st);
 cudaError_t launch_step(int prec, const StepArgs &a, cudaStream_t st);

@@ -46,4 +46,31 @@ __device__ __forceinline__ double noise_delta(uint64_t seed, uint64_t idx, uint6
     return (double)num * 0x1p-53;
 }
 
+// sigma = sigma0 (1 + a Delta) by the FP64 recipe, each operation rounded
+// on its own.
+__device__ __forceinline__ double sigma_f64(uint64_t seed, uint64_t idx, uint64_t step, int dist,
+                                            double sigma0, double amp)
+{
+    const double d = noise_delta(seed, idx, step, dist);
+    return __dmul_rn(sigma0, __dadd_rn(1.0, __dmul_rn(amp, d)));
+}
+
+// FP32 recipe of the same draw, for an FP32 state whose sigma is redrawn
+// every step (GB300's FP64 pipe is too slow to run the FP64 recipe per cell
+// per step): 24-bit integers j_a = w0 >> 8, j_b = w2 >> 8,
+//   dist 0:  Delta = (2 j_a - 2^24) 2^-24,   dist 1:  Delta = (j_a + j_b - 2^24) 2^-24,
+// exact in FP32, then sigma0 (1 + a Delta) with each operation rounded on
+// its own.
+__device__ __forceinline__ float sigma_f32(uint64_t seed, uint64_t idx, uint64_t step, int dist,
+                                           float sigma0, float amp)
+{
+    const uint4 w = philox4x32_10(
+        make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
+        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const int ja = (int)(w.x >> 8), jb = (int)(w.z >> 8);
+    const int num = dist == 0 ? 2 * ja - (1 << 24) : ja + jb - (1 << 24);
+    const float d = (float)num * 0x1p-24f;
+    return __fmul_rn(sigma0, __fadd_rn(1.0f, __fmul_rn(amp, d)));
+}
+
 }  // namespace cx

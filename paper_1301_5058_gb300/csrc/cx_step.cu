@@ -1,16 +1,27 @@
-// cx_step.cu -- one fused forward-Euler step of the bacteria/nutrient system
+// cx_step.cu -- one fused explicit step of the bacteria/nutrient system
 // (Eq. ka-chem-model in the general form of Eq. ka-model-dim, chemotactic
 // flux of Eq. chemflux, no-flux walls of Eq. bconds).
 //
-// One pass per step reads b, n, sigma and writes b', n'
+// One pass per forward-Euler step reads b, n, sigma and writes b', n'
 // (20 B per cell in FP32, 40 B in FP64).  Each thread owns 4 adjacent cells
 // of a row (one 16-byte vector per FP32 field) and marches down kRows rows,
-// keeping the row below in registers, so every cell is loaded from HBM once
+// keeping the row ahead in registers, so every cell is loaded from HBM once
 // and every y-face flux is evaluated once and reused by the two cells that
 // share it.  x-neighbours come from the adjacent lanes by warp shuffles;
 // lanes 0 and 31 fetch the one cell beyond the warp.  Boundary faces carry
 // zero flux.
+//
+// Template switches:
+//   NOISE 0  sigma read from its array (static field)
+//   NOISE 1  sigma regenerated in registers from Philox for the time step
+//            being taken (Sec. 3: redrawn at every grid point and step), so
+//            the pass reads only b and n (16 B per FP32 cell)
+//   STAGE 0  u_out = u + dt r(u): forward Euler, or Heun's first stage
+//   STAGE 1  Heun's second stage u_out = (u0 + u* + dt r(u*)) / 2, reading
+//            u0 pointwise and overwriting it in place (second-order
+//            Runge-Kutta, Sec. 3)
 #include "cx_internal.h"
+#include "cx_philox.cuh"
 
 namespace cx {
 namespace {
@@ -22,9 +33,16 @@ constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T> struct Vec;
 template <> struct Vec<float> {
+    // read-only path: for arrays no thread writes during the launch
     static __device__ __forceinline__ void load(const float *p, float (&v)[4])
     {
         const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    // coherent path: for the array the Heun combine overwrites in place
+    static __device__ __forceinline__ void load_rw(const float *p, float (&v)[4])
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
     static __device__ __forceinline__ void store(float *p, const float (&v)[4])
@@ -37,6 +55,12 @@ template <> struct Vec<double> {
     {
         const double2 q0 = __ldg(reinterpret_cast<const double2 *>(p));
         const double2 q1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+    static __device__ __forceinline__ void load_rw(const double *p, double (&v)[4])
+    {
+        const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
         v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
     }
     static __device__ __forceinline__ void store(double *p, const double (&v)[4])
@@ -53,6 +77,27 @@ __device__ __forceinline__ double div_w(double c, double q) { return c / q; }
 
 template <typename T> struct CoefT {
     T cA, cChi, cG, cR, cN;
+};
+
+// Per-step noise: the sigma recipe of the state's precision.
+template <typename T> struct NoiseT;
+template <> struct NoiseT<float> {
+    uint64_t seed, step;
+    int dist;
+    float sigma0, amp;
+    __device__ __forceinline__ float at(long long idx) const
+    {
+        return sigma_f32(seed, (uint64_t)idx, step, dist, sigma0, amp);
+    }
+};
+template <> struct NoiseT<double> {
+    uint64_t seed, step;
+    int dist;
+    double sigma0, amp;
+    __device__ __forceinline__ double at(long long idx) const
+    {
+        return sigma_f64(seed, (uint64_t)idx, step, dist, sigma0, amp);
+    }
 };
 
 // Scaled fluxes (phi, g) through the face between L (left/lower) and R.
@@ -79,19 +124,32 @@ __device__ __forceinline__ void face(T sL, T sR, T nL, T nR, T bL, T bR, const C
 
 template <typename T> struct Row {
     T b[kCells], n[kCells], s[kCells];
-    T hb, hn, hs;  // lane 0: cell x0-1; lane 31: cell x0+4
+    T hb, hn, hs;              // lane 0: cell x0-1; lane 31: cell x0+4
+    T ub[kCells], un[kCells];  // STAGE 1: the state at the start of the step
 };
 
-template <typename T, int LAW, int MOB>
-__global__ void __launch_bounds__(kThreads)
-    step_kernel(const T *__restrict__ b, const T *__restrict__ n, const T *__restrict__ s,
-                T *__restrict__ bo, T *__restrict__ no, int nx, int ny, long long pitch,
-                CoefT<T> k)
+template <typename T> struct Ptrs {
+    const T *__restrict__ b;
+    const T *__restrict__ n;
+    const T *__restrict__ s;
+    const T *bu;  // may alias bo (in-place Heun combine)
+    const T *nu;
+    T *bo;
+    T *no;
+};
+
+// One thread's march over rows j0..jend-1 in direction DIR (+1: increasing j,
+// -1: decreasing j).  The y-face shared with the row processed before
+// ("behind") is carried in registers; the y-face with the next row in march
+// order ("ahead") is computed from the row loaded in this iteration.  Face
+// values do not depend on DIR (a face is always evaluated with L the lower
+// row), so both directions give bit-identical results.
+template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR>
+__device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long long pitch,
+                                      const CoefT<T> &k, const NoiseT<T> &nz, int x0, int j0,
+                                      int jend)
 {
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * kThreads + threadIdx.x) * kCells;
-    const int j0 = blockIdx.y * kRows;
-    const int jend = min(j0 + kRows, ny);
     // threads past the right edge keep running (they take part in the
     // shuffles) but load an in-row vector and store nothing
     const long long xv = min((long long)x0, pitch - kCells);
@@ -100,37 +158,57 @@ __global__ void __launch_bounds__(kThreads)
     const bool halo = halo_l || halo_r;
     const long long xh = halo_l ? (long long)x0 - 1 : (long long)x0 + kCells;
 
-    auto load_row = [&](int r, Row<T> &R) {
+    auto load_row = [&](int r, Row<T> &R, bool own) {
         const long long off = (long long)r * pitch;
-        Vec<T>::load(b + off + xv, R.b);
-        Vec<T>::load(n + off + xv, R.n);
-        Vec<T>::load(s + off + xv, R.s);
+        Vec<T>::load(P.b + off + xv, R.b);
+        Vec<T>::load(P.n + off + xv, R.n);
+        if (NOISE == 0) {
+            Vec<T>::load(P.s + off + xv, R.s);
+        } else {
+            const long long row0 = (long long)r * nx;
+#pragma unroll
+            for (int c = 0; c < kCells; ++c)
+                R.s[c] = (x0 + c < nx) ? nz.at(row0 + x0 + c) : T(0);
+        }
         R.hb = R.hn = R.hs = T(0);
         if (halo) {
-            R.hb = __ldg(b + off + xh);
-            R.hn = __ldg(n + off + xh);
-            R.hs = __ldg(s + off + xh);
+            R.hb = __ldg(P.b + off + xh);
+            R.hn = __ldg(P.n + off + xh);
+            R.hs = NOISE == 0 ? __ldg(P.s + off + xh) : nz.at((long long)r * nx + xh);
+        }
+        if (STAGE == 1 && own) {
+            Vec<T>::load_rw(P.bu + off + xv, R.ub);
+            Vec<T>::load_rw(P.nu + off + xv, R.un);
         }
     };
-
-    Row<T> cur, nxt;
-    T phiS[kCells], gS[kCells];
-    load_row(j0, cur);
-    if (j0 > 0) {
-        Row<T> prv;
-        load_row(j0 - 1, prv);
+    // y-face between a lower row lo and an upper row hi
+    auto yface = [&](const Row<T> &lo, const Row<T> &hi, T (&ph)[kCells], T (&g)[kCells]) {
 #pragma unroll
         for (int c = 0; c < kCells; ++c)
-            face<T, LAW, MOB>(prv.s[c], cur.s[c], prv.n[c], cur.n[c], prv.b[c], cur.b[c], k,
-                              phiS[c], gS[c]);
+            face<T, LAW, MOB>(lo.s[c], hi.s[c], lo.n[c], hi.n[c], lo.b[c], hi.b[c], k, ph[c], g[c]);
+    };
+
+    const int jfirst = DIR > 0 ? j0 : jend - 1;
+    const int jbehind = jfirst - DIR;
+    Row<T> cur, nxt;
+    T phB[kCells], gB[kCells];
+    load_row(jfirst, cur, true);
+    if (jbehind >= 0 && jbehind < ny) {
+        Row<T> prv;
+        load_row(jbehind, prv, false);
+        if (DIR > 0) yface(prv, cur, phB, gB);
+        else yface(cur, prv, phB, gB);
     } else {
 #pragma unroll
-        for (int c = 0; c < kCells; ++c) phiS[c] = gS[c] = T(0);
+        for (int c = 0; c < kCells; ++c) phB[c] = gB[c] = T(0);  // wall behind
     }
 
-    for (int j = j0; j < jend; ++j) {
-        const bool has_up = (j + 1 < ny);  // uniform across the block
-        if (has_up) load_row(j + 1, nxt);
+    const int rows = jend - j0;
+    for (int it = 0; it < rows; ++it) {
+        const int j = jfirst + DIR * it;
+        const int ja = j + DIR;
+        const bool has_a = (ja >= 0 && ja < ny);  // uniform across the block
+        if (has_a) load_row(ja, nxt, it + 1 < rows);
 
         // x-neighbours of this thread's 4 cells
         T lb = __shfl_up_sync(kFull, cur.b[kCells - 1], 1);
@@ -156,65 +234,101 @@ __global__ void __launch_bounds__(kThreads)
         for (int c = 1; c <= kCells; ++c)
             if (x0 + c >= nx) phX[c] = gX[c] = T(0);  // east wall (and padding)
 
-        // y-faces between this row and the next
-        T phiN[kCells], gN[kCells];
+        // y-face with the row ahead (a wall past the grid's first/last row)
+        T phA[kCells], gA[kCells];
+        if (has_a) {
+            if (DIR > 0) yface(cur, nxt, phA, gA);
+            else yface(nxt, cur, phA, gA);
+        } else {
 #pragma unroll
-        for (int c = 0; c < kCells; ++c) {
-            if (has_up)
-                face<T, LAW, MOB>(cur.s[c], nxt.s[c], cur.n[c], nxt.n[c], cur.b[c], nxt.b[c], k,
-                                  phiN[c], gN[c]);
-            else
-                phiN[c] = gN[c] = T(0);  // north wall
+            for (int c = 0; c < kCells; ++c) phA[c] = gA[c] = T(0);
         }
 
         T ob[kCells], on[kCells];
 #pragma unroll
         for (int c = 0; c < kCells; ++c) {
+            const T phN = DIR > 0 ? phA[c] : phB[c], phS = DIR > 0 ? phB[c] : phA[c];
+            const T gN = DIR > 0 ? gA[c] : gB[c], gS = DIR > 0 ? gB[c] : gA[c];
             const T r = cur.n[c] * cur.b[c];
-            const T divb = (phX[c + 1] - phX[c]) + (phiN[c] - phiS[c]);
-            const T divn = (gX[c + 1] - gX[c]) + (gN[c] - gS[c]);
+            const T divb = (phX[c + 1] - phX[c]) + (phN - phS);
+            const T divn = (gX[c + 1] - gX[c]) + (gN - gS);
             ob[c] = (cur.b[c] + divb) + k.cR * r;
             on[c] = (cur.n[c] + divn) - k.cN * r;
+            if (STAGE == 1) {
+                ob[c] = T(0.5) * (cur.ub[c] + ob[c]);
+                on[c] = T(0.5) * (cur.un[c] + on[c]);
+            }
         }
         const long long off = (long long)j * pitch;
         if (x0 + kCells <= nx) {
-            Vec<T>::store(bo + off + x0, ob);
-            Vec<T>::store(no + off + x0, on);
+            Vec<T>::store(P.bo + off + x0, ob);
+            Vec<T>::store(P.no + off + x0, on);
         } else {
 #pragma unroll
             for (int c = 0; c < kCells; ++c)
                 if (x0 + c < nx) {
-                    bo[off + x0 + c] = ob[c];
-                    no[off + x0 + c] = on[c];
+                    P.bo[off + x0 + c] = ob[c];
+                    P.no[off + x0 + c] = on[c];
                 }
         }
 
         cur = nxt;
 #pragma unroll
-        for (int c = 0; c < kCells; ++c) { phiS[c] = phiN[c]; gS[c] = gN[c]; }
+        for (int c = 0; c < kCells; ++c) { phB[c] = phA[c]; gB[c] = gA[c]; }
     }
 }
 
-template <typename T, int LAW, int MOB>
+// Row-bands alternate their march direction, so a halo row shared by two
+// neighbouring bands is read by both near the start (or both near the end)
+// of their marches, while it is still in L2, instead of once at the start
+// of one band and again at the end of the other.
+template <typename T, int LAW, int MOB, int NOISE, int STAGE>
+__global__ void __launch_bounds__(kThreads)
+    step_kernel(Ptrs<T> P, int nx, int ny, long long pitch, CoefT<T> k, NoiseT<T> nz)
+{
+    const int x0 = (blockIdx.x * kThreads + threadIdx.x) * kCells;
+    const int j0 = blockIdx.y * kRows;
+    const int jend = min(j0 + kRows, ny);
+    if (blockIdx.y & 1)
+        march<T, LAW, MOB, NOISE, STAGE, -1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    else
+        march<T, LAW, MOB, NOISE, STAGE, +1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+}
+
+template <typename T, int LAW, int MOB, int NOISE, int STAGE>
 cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
 {
     const CoefT<T> k{(T)a.k.cA, (T)a.k.cChi, (T)a.k.cG, (T)a.k.cR, (T)a.k.cN};
+    NoiseT<T> nz;
+    nz.seed = a.sg.seed;
+    nz.step = (uint64_t)a.step;
+    nz.dist = a.sg.dist;
+    nz.sigma0 = (T)a.sg.sigma0;
+    nz.amp = (T)a.sg.amp;
+    Ptrs<T> P{(const T *)a.b, (const T *)a.n, (const T *)a.s, (const T *)a.bu,
+              (const T *)a.nu, (T *)a.bo, (T *)a.no};
     const dim3 grid((a.nx + kThreads * kCells - 1) / (kThreads * kCells),
                     (a.ny + kRows - 1) / kRows);
-    step_kernel<T, LAW, MOB><<<grid, kThreads, 0, st>>>(
-        (const T *)a.b, (const T *)a.n, (const T *)a.s, (T *)a.bo, (T *)a.no, a.nx, a.ny, a.pitch,
-        k);
+    step_kernel<T, LAW, MOB, NOISE, STAGE><<<grid, kThreads, 0, st>>>(P, a.nx, a.ny, a.pitch, k, nz);
     return cudaGetLastError();
+}
+
+template <typename T, int LAW, int MOB>
+cudaError_t launch_ns(const StepArgs &a, cudaStream_t st)
+{
+    if (a.sg.per_step)
+        return a.stage ? launch_t<T, LAW, MOB, 1, 1>(a, st) : launch_t<T, LAW, MOB, 1, 0>(a, st);
+    return a.stage ? launch_t<T, LAW, MOB, 0, 1>(a, st) : launch_t<T, LAW, MOB, 0, 0>(a, st);
 }
 
 template <typename T>
 cudaError_t launch_prec(const StepArgs &a, cudaStream_t st)
 {
     if (a.law == CX_CHEMO_RECEPTOR)
-        return a.mob == CX_MOBILITY_CENTRAL ? launch_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(a, st)
-                                            : launch_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(a, st);
-    return a.mob == CX_MOBILITY_CENTRAL ? launch_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(a, st)
-                                        : launch_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(a, st);
+        return a.mob == CX_MOBILITY_CENTRAL ? launch_ns<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(a, st)
+                                            : launch_ns<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(a, st);
+    return a.mob == CX_MOBILITY_CENTRAL ? launch_ns<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(a, st)
+                                        : launch_ns<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(a, st);
 }
 
 }  // namespace

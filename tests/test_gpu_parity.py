@@ -321,3 +321,82 @@ def test_full_size_fp32_sampled_windows(cx):
         b1 = sim.field(cx.CX_FIELD_B, np.float32)
         n1 = sim.field(cx.CX_FIELD_N, np.float32)
     assert _window_error(cfg, dt, s, b0, n0, b1, n1, centre + edges) <= 2e-6
+
+
+# ---------------------------------------------------------------------------
+# The paper's own scheme (Sec. 3): second-order Runge-Kutta (Heun) and sigma
+# redrawn from a triangular law at every grid point and time step.
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_per_step_sigma_is_bit_exact(cx, prec):
+    cfg = dict(W.CONFIG0, nx=130, ny=70, noise_mode=1, noise_dist=1, noise_amp=1.0, seed=21)
+    recipe = oracle.sigma_field if prec == 0 else oracle.sigma_field_f32
+    with make_sim(cx, cfg, prec)[0] as sim:
+        for k in (0, 3):
+            sim.step(k)
+            step = cx.cx_get_time(sim.h)[0]
+            ref = recipe(130, 70, 21, cfg["sigma0"], 1.0, dist=1, step=step)
+            assert np.array_equal(sim.field(cx.CX_FIELD_SIGMA), ref)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("noise_mode", [0, 1])
+def test_fp64_parity_scheme_and_noise(cx, scheme, noise_mode):
+    cfg = dict(W.CONFIG0, nx=150, ny=131, chi0=1.0, scheme=scheme, noise_mode=noise_mode,
+               noise_dist=1, noise_amp=1.0, seed=5)
+    s, b, n = oracle_inputs(cfg)
+    with make_sim(cx, cfg, cx.CX_PREC_F64)[0] as sim:
+        sim.set_field(cx.CX_FIELD_B, b)
+        sim.set_field(cx.CX_FIELD_N, n)
+        sim.step(400)
+        gb, gn = sim.field(cx.CX_FIELD_B), sim.field(cx.CX_FIELD_N)
+    ob, on, _ = oracle.run(s, b, n, 400, dx=1.0, dt=oracle_dt(cfg), Dn=1.0, theta=1.0, chi0=1.0,
+                           scheme=scheme, noise_mode=noise_mode, seed=5, sigma0=cfg["sigma0"],
+                           amp=1.0, dist=1, recipe=0)
+    assert rel_l2(gb, ob) <= TOL64 and rel_l2(gn, on) <= TOL64, (rel_l2(gb, ob), rel_l2(gn, on))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_fp32_parity_paper_scheme(cx, scheme):
+    cfg = dict(W.CONFIG0, nx=200, ny=190, chi0=1.0, scheme=scheme, noise_mode=1, noise_dist=1,
+               noise_amp=1.0, seed=8)
+    s, b, n = oracle_inputs(cfg)
+    with make_sim(cx, cfg, cx.CX_PREC_F32)[0] as sim:
+        sim.step(1000)
+        gb, gn = sim.field(cx.CX_FIELD_B), sim.field(cx.CX_FIELD_N)
+    ob, on, _ = oracle.run(s, b, n, 1000, dx=1.0, dt=oracle_dt(cfg), Dn=1.0, theta=1.0, chi0=1.0,
+                           scheme=scheme, noise_mode=1, seed=8, sigma0=cfg["sigma0"], amp=1.0,
+                           dist=1, recipe=1)
+    assert rel_l2(gb, ob) <= TOL32 and rel_l2(gn, on) <= TOL32
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (7, 5), (513, 70), (1030, 33)])
+def test_fp64_heun_ragged_shapes(cx, nx, ny):
+    cfg = dict(W.CONFIG0, nx=nx, ny=ny, chi0=1.5, scheme=1, noise_mode=1, noise_dist=1, seed=nx + ny)
+    b, n = W.perturbed_fields(nx, ny, seed=cfg["seed"])
+    with make_sim(cx, cfg, cx.CX_PREC_F64)[0] as sim:
+        sim.set_field(cx.CX_FIELD_B, b)
+        sim.set_field(cx.CX_FIELD_N, n)
+        sim.step(30)
+        gb, gn = sim.field(cx.CX_FIELD_B), sim.field(cx.CX_FIELD_N)
+    ob, on, _ = oracle.run(np.zeros((ny, nx)), b, n, 30, dx=1.0, dt=oracle_dt(cfg), Dn=1.0,
+                           theta=1.0, chi0=1.5, scheme=1, noise_mode=1, seed=cfg["seed"],
+                           sigma0=cfg["sigma0"], amp=cfg["noise_amp"], dist=1, recipe=0)
+    assert rel_l2(gb, ob) <= TOL64 and rel_l2(gn, on) <= TOL64
+
+
+def test_heun_conserves_and_resumes_bitwise(cx, tmp_path):
+    cfg = dict(W.CONFIG0, nx=120, ny=100, scheme=1, noise_mode=1, noise_dist=1, theta=0.8)
+    for prec, tol in ((0, 1e-12), (1, 2e-6)):
+        with make_sim(cx, cfg, prec)[0] as a, make_sim(cx, cfg, prec)[0] as b:
+            d0 = a.diagnostics()
+            a.step(500)
+            d1 = a.diagnostics()
+            assert abs(d1["invariant"] - d0["invariant"]) <= tol * d0["invariant"]
+            b.step(200)
+            path = str(tmp_path / f"h{prec}.ckpt")
+            cx.cx_save(b.h, path)
+            with cx.Sim.load(path) as c:
+                c.step(300)
+                for w in (cx.CX_FIELD_B, cx.CX_FIELD_N):
+                    assert np.array_equal(a.field(w), c.field(w))

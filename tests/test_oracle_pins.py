@@ -344,3 +344,26 @@ def test_c_bar_monotone_in_chi0():
         v = [speed.c_bar(n0, chi0, 1.0) for chi0 in np.linspace(0, 10, 101)]
         assert all(b >= a for a, b in zip(v, v[1:]))
     assert speed.b_star(1.0, 1e-9) == pytest.approx(1 / 3, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# FP32 recipe of the per-step noise
+
+@pytest.mark.parametrize("dist", [0, 1])
+def test_fp32_noise_recipe_tracks_the_fp64_recipe(dist):
+    # the 24-bit uniforms are the top bits of the 53-bit ones, so Delta moves
+    # by less than 2^-23, and three float roundings add at most 3 ulp
+    s0, a = 4.0, 0.8
+    s64 = oracle.sigma_field(300, 200, 11, s0, a, dist=dist, step=5)
+    s32 = oracle.sigma_field_f32(300, 200, 11, s0, a, dist=dist, step=5)
+    assert np.all(s32 == s32.astype(np.float32))           # exactly float values
+    bound = s0 * (a * 2.0 ** -23 + 4 * 2.0 ** -24 * (1 + a))
+    assert np.max(np.abs(s32 - s64)) <= bound
+    d = np.sort(((s32 / s0 - 1) / a).ravel())
+    if dist == 1:
+        F = np.where(d <= 0, 0.5 * (1 + d) ** 2, 1 - 0.5 * (1 - d) ** 2)
+    else:
+        F = 0.5 * (1 + d)
+    m = d.size
+    ks = np.max(np.maximum(np.arange(1, m + 1) / m - F, F - np.arange(m) / m))
+    assert ks < 1.63 / math.sqrt(m) + 1e-6
