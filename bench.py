@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--dist", default="uniform", choices=["uniform", "triangular"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="grid", choices=["grid", "sweep"],
+                    help="grid: the 16384^2 single grid; sweep: the batched parameter sweep")
+    ap.add_argument("--count", type=int, default=512, help="sweep instances")
+    ap.add_argument("--point-steps", type=int, default=20000, help="time steps per sweep point")
+    ap.add_argument("--tune", action="store_true", help="autotune the batch before timing")
     return ap.parse_args()
 
 
@@ -279,6 +284,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.workload == "sweep":
+        return main_sweep(args)
 
     if world > 1:
         import torch
@@ -346,6 +353,95 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def main_sweep(args):
+    """Batched parameter sweep (512 instances, sides 512..2048, FP32): sweep
+    points per hour of the batch, and of the same points stepped one
+    simulation at a time through cx_step (both measured in this run; each
+    point is `--point-steps` time steps plus its creation)."""
+    import torch
+
+    import paper_1301_5058_gb300 as cx
+    from paper_1301_5058_gb300 import autotune
+    from paper_1301_5058_gb300 import workloads as W
+
+    specs = W.sweep_specs(args.count, seed=0, steps=args.point_steps)
+    S, K, Wm = args.window, args.steps, args.warmup
+    cells = sum(s["nx"] * s["ny"] for s in specs)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = cx.Batch(specs)
+    create_s = time.perf_counter() - t0
+    cx.cx_batch_set_stream(bt.h, stream.cuda_stream)
+    bt._stream = stream
+    if args.tune:
+        autotune.tune_batch(bt, steps=64, reps=2, use_cache=False)
+    choice = cx.cx_batch_get_tuning(bt.h)
+
+    def timed(step_fn, diag_fn, clk=None):
+        for _ in range(Wm):
+            step_fn(S)
+            diag_fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for k in range(K):
+            evs[k][0].record(stream)
+            step_fn(S)
+            evs[k][1].record(stream)
+            diag_fn()
+        stop.record(stream)
+        stop.synchronize()
+        return start.elapsed_time(stop) / 1e3, sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    with ClockSampler(uuid) as clk:
+        elapsed, kernel_s = timed(bt.step, bt.diagnostics)
+    per_step = elapsed / (K * S)
+    batch_pph = args.count * 3600.0 / (args.point_steps * per_step + create_s)
+    bt.close()
+
+    # the same points, one simulation at a time (one per size class timed)
+    single = {}
+    for side in sorted({s["nx"] for s in specs}):
+        spec = next(s for s in specs if s["nx"] == side)
+        kw = {k: v for k, v in spec.items() if k not in ("nx", "ny", "dx", "seed")}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = cx.Sim(side, side, 1.0, seed=spec["seed"], **kw)
+        c_s = time.perf_counter() - t0
+        cx.cx_set_stream(sim.h, stream.cuda_stream)
+        el, _ = timed(sim.step, sim.diagnostics)
+        single[side] = (el / (K * S), c_s)
+        sim.close()
+    single_total = sum(args.point_steps * single[s["nx"]][0] + single[s["nx"]][1] for s in specs)
+    single_pph = args.count * 3600.0 / single_total
+    peak, peak_kind = peaks()
+    achieved = 20 * cells / (kernel_s / (K * S)) / 1e9
+    print(json.dumps({
+        "metric": "sweep points/hour", "value": batch_pph, "unit": "points/h", "n_gpus": 1,
+        "steps": K, "warmup": Wm, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched sweep: {args.count} instances, sides from "
+                               f"{sorted(set(s['nx'] for s in specs))}, (n0, chi0, sigma0) log grid, "
+                               f"static uniform noise a=0.5, forward Euler, {args.point_steps} steps "
+                               f"per point", "cells_per_time_step": cells,
+                   "time_steps_per_step": S, "tuning": {"tile_rows": choice[0], "graph_steps": choice[1],
+                                                        "group_bytes": choice[2]}},
+        "cell_updates_per_s": cells / per_step,
+        "single_instance_points_per_hour": single_pph,
+        "single_instance_ms_per_time_step": {str(k): v[0] * 1e3 for k, v in single.items()},
+        "speedup_vs_single_instance": batch_pph / single_pph,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_cell": 20},
+        "gpu_launches": K * (S + 2),
+        "clocks": clk.summary(),
+    }))
 
 
 def main_reference(args, rank, world):

@@ -195,9 +195,17 @@ int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt);
 int cx_set_step(cx_ctx *c, int64_t step);
 
 /* Number of time steps fused per launch (temporal blocking depth), 1..8.
- * Results do not depend on it bit for bit.  Default chosen per grid. */
+ * The result is bit-identical for every k.  Default 1. */
 int cx_set_time_block(cx_ctx *c, int32_t k);
 int cx_get_time_block(cx_ctx *c, int32_t *k);
+
+/* Height in rows of one step-kernel tile (each CTA marches one tile of
+ * 512 columns x rows), 1..4096 with ceil(ny/rows) <= 65535; a performance
+ * knob that the autotuner sets.  The result is bit-identical for every
+ * value.  Default: 32, or fewer on small grids so that about four tiles
+ * per SM are launched. */
+int cx_set_tile_rows(cx_ctx *c, int32_t rows);
+int cx_get_tile_rows(cx_ctx *c, int32_t *rows);
 
 /* Write / read a checkpoint: header (grid, params, seed, step, dt,
  * precision) and the raw b, n and sigma arrays.  A run resumed from a
@@ -208,6 +216,57 @@ int cx_load(const char *path, cx_ctx **out);
 
 /* Free the handle and its device buffers.  NULL is a no-op. */
 void cx_destroy(cx_ctx *c);
+
+/* ---- many simulations at once (parameter sweeps) --------------------------
+ *
+ * A batch holds `count` independent simulations of the same system with
+ * their own grid size, parameters (n0, chi0, sigma0, a, ...) and seed, as in
+ * the parameter study of Sec. 3 (Table tabresparam).  All instances share
+ * precision, scheme, chemo_law and mobility; noise must be CX_NOISE_STATIC.
+ * An instance evolves bit for bit as a cx_ctx created with the same grid,
+ * parameters and seed.  A batch owns a non-default CUDA stream. */
+
+/* Allocate and initialise `count` instances (1..65535); grids[i],
+ * params[i], seeds[i] describe instance i.  Synchronous.  Errors:
+ * INVALID_ARG, DT_UNSTABLE, UNSUPPORTED (per-step noise), OOM, CUDA. */
+int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params,
+                    const uint64_t *seeds, cx_batch **out);
+
+/* Run later work on `stream` (a non-default cudaStream_t). */
+int cx_batch_set_stream(cx_batch *b, void *stream);
+
+/* Performance knobs, none of which changes any result bit:
+ *   tile_rows   rows per tile of the step kernel (1..4096, default 32);
+ *   graph_steps steps captured per CUDA graph and replayed (0: plain
+ *               launches; rounded up to even for Euler; default 64);
+ *   group_bytes if > 0, instances are cut into consecutive groups whose
+ *               fields fit this many bytes and each group runs all its steps
+ *               before the next starts (keeps a group resident in L2);
+ *               0: every launch covers every instance (default). */
+int cx_batch_set_tuning(cx_batch *b, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes);
+int cx_batch_get_tuning(cx_batch *b, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes);
+
+/* Advance every instance by n_steps >= 0 steps.  Asynchronous. */
+int cx_batch_step(cx_batch *b, int64_t n_steps);
+int cx_batch_synchronize(cx_batch *b);
+
+/* Diagnostics of every instance into out[0..count-1] (FP64 sums; the
+ * summation order differs from cx_diagnostics, so sums agree to round-off).
+ * Synchronises.  Returns NONFINITE / NEGATIVE (out filled, per-instance
+ * status set) if an instance is unhealthy. */
+int cx_batch_diagnostics(cx_batch *b, cx_diag *out);
+
+/* Field I/O of instance `index` (same rules as cx_get_field/cx_set_field). */
+int cx_batch_get_field(cx_batch *b, int32_t index, int32_t which, void *host, int32_t dtype,
+                       size_t count);
+int cx_batch_set_field(cx_batch *b, int32_t index, int32_t which, const void *host,
+                       int32_t dtype, size_t count);
+
+/* Number of instances and steps taken. */
+int cx_batch_get_time(cx_batch *b, int32_t *count, int64_t *step);
+
+/* Free the batch.  NULL is a no-op. */
+void cx_batch_destroy(cx_batch *b);
 
 /* ---- diagnostics without any allocation --------------------------------- */
 

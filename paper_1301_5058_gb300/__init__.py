@@ -94,6 +94,26 @@ _SIGNATURES = {
     "cx_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "cx_destroy": (None, [_P]),
+    "cx_set_tile_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cx_get_tile_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "cx_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(cx_grid),
+                                       ctypes.POINTER(cx_params), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(_P)]),
+    "cx_batch_set_stream": (ctypes.c_int, [_P, _P]),
+    "cx_batch_set_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]),
+    "cx_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "cx_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cx_batch_synchronize": (ctypes.c_int, [_P]),
+    "cx_batch_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(cx_diag)]),
+    "cx_batch_get_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                          ctypes.c_size_t]),
+    "cx_batch_set_field": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                          ctypes.c_size_t]),
+    "cx_batch_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "cx_batch_destroy": (None, [_P]),
     "cx_diagnostics_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _P, _P,
@@ -231,6 +251,82 @@ def cx_get_time_block(h) -> int:
     return k.value
 
 
+def cx_set_tile_rows(h, rows: int):
+    _check(lib().cx_set_tile_rows(h, rows))
+
+
+def cx_get_tile_rows(h) -> int:
+    r = ctypes.c_int32()
+    _check(lib().cx_get_tile_rows(h, ctypes.byref(r)))
+    return r.value
+
+
+def cx_batch_create(grids, params, seeds) -> int:
+    n = len(grids)
+    if not (len(params) == len(seeds) == n):
+        raise ValueError("grids, params and seeds must have the same length")
+    G = (cx_grid * n)(*grids)
+    Pm = (cx_params * n)(*params)
+    S = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+    h = _P()
+    _check(lib().cx_batch_create(n, G, Pm, S, ctypes.byref(h)))
+    return h.value
+
+
+def cx_batch_set_stream(h, stream: int):
+    _check(lib().cx_batch_set_stream(h, stream))
+
+
+def cx_batch_set_tuning(h, tile_rows: int, graph_steps: int, group_bytes: int):
+    _check(lib().cx_batch_set_tuning(h, tile_rows, graph_steps, group_bytes))
+
+
+def cx_batch_get_tuning(h):
+    r, g, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().cx_batch_get_tuning(h, ctypes.byref(r), ctypes.byref(g), ctypes.byref(b)))
+    return r.value, g.value, b.value
+
+
+def cx_batch_step(h, n_steps: int):
+    _check(lib().cx_batch_step(h, n_steps))
+
+
+def cx_batch_synchronize(h):
+    _check(lib().cx_batch_synchronize(h))
+
+
+def cx_batch_get_time(h):
+    c, s = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().cx_batch_get_time(h, ctypes.byref(c), ctypes.byref(s)))
+    return c.value, s.value
+
+
+def cx_batch_diagnostics(h, check: bool = True):
+    count, _ = cx_batch_get_time(h)
+    out = (cx_diag * count)()
+    rc = lib().cx_batch_diagnostics(h, out)
+    if check or rc not in (CX_OK, CX_ERR_NONFINITE, CX_ERR_NEGATIVE):
+        _check(rc)
+    return [d.as_dict() for d in out]
+
+
+def cx_batch_get_field(h, index: int, which: int, out: np.ndarray) -> np.ndarray:
+    if not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be C-contiguous")
+    _check(lib().cx_batch_get_field(h, index, which, out.ctypes.data, _host_view(out), out.size))
+    return out
+
+
+def cx_batch_set_field(h, index: int, which: int, src: np.ndarray):
+    src = np.ascontiguousarray(src)
+    _check(lib().cx_batch_set_field(h, index, which, src.ctypes.data, _host_view(src), src.size))
+
+
+def cx_batch_destroy(h):
+    if h:
+        lib().cx_batch_destroy(h)
+
+
 def cx_save(h, path: str):
     _check(lib().cx_save(h, os.fsencode(path)))
 
@@ -298,6 +394,53 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             cx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent simulations stepped together.  ``specs`` is a list of
+    dicts with keys nx, ny, dx, seed and any cx_params field."""
+
+    def __init__(self, specs):
+        self.grids = [cx_grid(s["nx"], s["ny"], s.get("dx", 1.0)) for s in specs]
+        self.params = [cx_params_default(**{k: v for k, v in s.items()
+                                            if k not in ("nx", "ny", "dx", "seed")}) for s in specs]
+        self.h = cx_batch_create(self.grids, self.params, [s.get("seed", 0) for s in specs])
+
+    def __len__(self):
+        return len(self.grids)
+
+    def step(self, n):
+        cx_batch_step(self.h, n)
+
+    def diagnostics(self, check=True):
+        return cx_batch_diagnostics(self.h, check=check)
+
+    def field(self, index, which, dtype=np.float64):
+        g = self.grids[index]
+        return cx_batch_get_field(self.h, index, which, np.empty((g.ny, g.nx), dtype))
+
+    def set_field(self, index, which, arr):
+        cx_batch_set_field(self.h, index, which, arr)
+
+    def tune(self, tile_rows, graph_steps, group_bytes):
+        cx_batch_set_tuning(self.h, tile_rows, graph_steps, group_bytes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cx_batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -99,17 +99,20 @@ double b_threshold_of(const cx_params *p)
     return p->b_threshold > 0.0 ? p->b_threshold : 0.1 * p->theta * p->n0;
 }
 
-cx::Coef coef_of(const cx_ctx *c)
+int resolve_dt(const cx_grid *g, const cx_params *p, double *dt)
 {
-    const double dx2 = c->g.dx * c->g.dx;
-    cx::Coef k;
-    k.cA = c->dt / (8.0 * dx2);
-    k.cChi = c->p.chemo_law == CX_CHEMO_RECEPTOR ? 2.0 * c->p.chi0 : 0.5 * c->p.chi0;
-    k.cG = c->dt * c->p.Dn / dx2;
-    k.cR = c->dt * c->p.theta;
-    k.cN = c->dt;
-    return k;
+    const double lim = dt_limit_of(g, p);
+    if (p->dt == 0.0) {
+        *dt = p->cfl_frac * lim;
+    } else {
+        if (p->dt > lim)
+            return fail(CX_ERR_DT_UNSTABLE, "dt = %.17g exceeds the stability limit %.17g", p->dt, lim);
+        *dt = p->dt;
+    }
+    return CX_OK;
 }
+
+cx::Coef coef_of(const cx_ctx *c) { return cx::make_coef(c->g, c->p, c->dt); }
 
 void free_buffers(cx_ctx *c)
 {
@@ -142,6 +145,16 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     c->pitch = ((long long)g->nx + align - 1) / align * align;
     c->dt = dt;
     c->time_block = 1;
+    // default tile height: 32 rows, or fewer so that a small grid still
+    // launches about four 512-column tiles per SM (152 SMs) instead of a
+    // handful of long, latency-bound marches
+    {
+        const long long tiles_x = ((long long)g->nx + 511) / 512;
+        long long rows = ((long long)g->ny * tiles_x + 4 * 152 - 1) / (4 * 152);
+        rows = rows < 1 ? 1 : (rows > 32 ? 32 : rows);
+        while (((long long)g->ny + rows - 1) / rows > 65535) ++rows;
+        c->tile_rows = (int)rows;
+    }
     c->stream = nullptr;
     cudaGetDevice(&c->device);
     const size_t bytes = (size_t)c->pitch * (size_t)g->ny * c->elem;
@@ -202,6 +215,20 @@ cudaError_t fill_sigma(cx_ctx *c, int64_t step)
 }  // namespace
 
 int cx::record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+int cx::validate_params(const cx_grid *g, const cx_params *p) { return validate(g, p); }
+int cx::resolve_time_step(const cx_grid *g, const cx_params *p, double *dt) { return resolve_dt(g, p, dt); }
+double cx::envelope_level(const cx_params &p) { return b_threshold_of(&p); }
+cx::Coef cx::make_coef(const cx_grid &g, const cx_params &p, double dt)
+{
+    const double dx2 = g.dx * g.dx;
+    cx::Coef k;
+    k.cA = dt / (8.0 * dx2);
+    k.cChi = p.chemo_law == CX_CHEMO_RECEPTOR ? 2.0 * p.chi0 : 0.5 * p.chi0;
+    k.cG = dt * p.Dn / dx2;
+    k.cR = dt * p.theta;
+    k.cN = dt;
+    return k;
+}
 
 extern "C" {
 
@@ -259,19 +286,6 @@ int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit)
     return CX_OK;
 }
 
-static int resolve_dt(const cx_grid *g, const cx_params *p, double *dt)
-{
-    const double lim = dt_limit_of(g, p);
-    if (p->dt == 0.0) {
-        *dt = p->cfl_frac * lim;
-    } else {
-        if (p->dt > lim)
-            return fail(CX_ERR_DT_UNSTABLE, "dt = %.17g exceeds the stability limit %.17g", p->dt, lim);
-        *dt = p->dt;
-    }
-    return CX_OK;
-}
-
 int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
 {
     if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
@@ -316,6 +330,7 @@ int cx_step(cx_ctx *c, int64_t n_steps)
     a.pitch = c->pitch;
     a.law = c->p.chemo_law;
     a.mob = c->p.mobility;
+    a.rows = c->tile_rows;
     a.k = coef_of(c);
     a.sg.per_step = c->p.noise_mode == CX_NOISE_PER_STEP;
     a.sg.dist = c->p.noise_dist;
@@ -518,6 +533,26 @@ int cx_set_time_block(cx_ctx *c, int32_t k)
     if (rc) return rc;
     if (k < 1 || k > 8) return fail(CX_ERR_INVALID_ARG, "time block %d outside 1..8", k);
     c->time_block = k;
+    return CX_OK;
+}
+
+int cx_set_tile_rows(cx_ctx *c, int32_t rows)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (rows < 1 || rows > 4096 || ((long long)c->g.ny + rows - 1) / rows > 65535)
+        return fail(CX_ERR_INVALID_ARG, "tile rows %d outside 1..4096 or too small for ny = %d",
+                    rows, c->g.ny);
+    c->tile_rows = rows;
+    return CX_OK;
+}
+
+int cx_get_tile_rows(cx_ctx *c, int32_t *rows)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!rows) return fail(CX_ERR_INVALID_ARG, "rows must not be NULL");
+    *rows = c->tile_rows;
     return CX_OK;
 }
 

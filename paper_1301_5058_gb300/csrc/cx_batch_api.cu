@@ -1,0 +1,487 @@
+// cx_batch_api.cu -- the cx_batch_* entry points (include/cx.h): a set of
+// independent simulations (one parameter sweep) stepped together by the
+// batched kernels of cx_batch.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cx_internal.h"
+
+namespace {
+
+int bfail(int code, const char *msg) { return cx::record_error(code, msg); }
+
+int bcuda(cudaError_t e, const char *what)
+{
+    char buf[300];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return cx::record_error(e == cudaErrorMemoryAllocation ? CX_ERR_OOM : CX_ERR_CUDA, buf);
+}
+
+#define BX_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return bcuda(e_, (what));     \
+    } while (0)
+
+constexpr int kTileCols = 512;       // columns per tile (128 threads x 4 cells)
+constexpr int kDiagBlocksPerInst = 64;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct cx_batch {
+    int count = 0, prec = 0, law = 0, mob = 0, scheme = 0;
+    std::vector<cx_grid> g;
+    std::vector<cx_params> p;
+    std::vector<uint64_t> seed;
+    std::vector<double> dt;
+    std::vector<long long> pitch;
+    std::vector<void *> fb[2], fn[2], fs;
+    std::vector<long long> footprint;  // device bytes of each instance's fields
+    void *arena = nullptr;
+    size_t elem = 4;
+    void *d_inst = nullptr;
+    std::vector<unsigned char> h_inst;
+    int4 *d_work = nullptr;
+    std::vector<int> work_begin;  // first work item of each instance (+ total)
+    int rows = 32;
+    int graph_steps = 64;
+    long long group_bytes = 0;
+    std::vector<int> group_first;  // instance index where each group starts (+ count)
+    std::vector<cudaGraphExec_t> gexec;
+    int cur = 0;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *d_part = nullptr, *d_res = nullptr, *h_res = nullptr;
+};
+
+namespace {
+
+void drop_graphs(cx_batch *B)
+{
+    for (auto &e : B->gexec)
+        if (e) cudaGraphExecDestroy(e);
+    B->gexec.clear();
+}
+
+void free_batch(cx_batch *B)
+{
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    drop_graphs(B);
+    if (B->arena) cudaFree(B->arena);
+    if (B->d_inst) cudaFree(B->d_inst);
+    if (B->d_work) cudaFree(B->d_work);
+    if (B->d_part) cudaFree(B->d_part);
+    if (B->d_res) cudaFree(B->d_res);
+    if (B->h_res) cudaFreeHost(B->h_res);
+    if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+// Tile work list for the current tile height, instance by instance.
+int build_work(cx_batch *B)
+{
+    std::vector<int4> w;
+    B->work_begin.assign(B->count + 1, 0);
+    for (int i = 0; i < B->count; ++i) {
+        B->work_begin[i] = (int)w.size();
+        const int tx = (B->g[i].nx + kTileCols - 1) / kTileCols;
+        const int ty = (B->g[i].ny + B->rows - 1) / B->rows;
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) w.push_back(make_int4(i, x, y, 0));
+    }
+    B->work_begin[B->count] = (int)w.size();
+    if (B->d_work) cudaFree(B->d_work);
+    B->d_work = nullptr;
+    BX_CUDA(cudaMalloc((void **)&B->d_work, w.size() * sizeof(int4)), "work list allocation");
+    BX_CUDA(cudaMemcpy(B->d_work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice),
+            "work list upload");
+    return CX_OK;
+}
+
+// Consecutive groups of instances whose fields fit group_bytes (one group
+// with every instance when group_bytes == 0; an instance larger than the
+// budget forms a group of its own).
+void build_groups(cx_batch *B)
+{
+    B->group_first.clear();
+    long long acc = 0;
+    for (int i = 0; i < B->count; ++i) {
+        if (i == 0 || (B->group_bytes > 0 && acc + B->footprint[i] > B->group_bytes)) {
+            B->group_first.push_back(i);
+            acc = 0;
+        }
+        acc += B->footprint[i];
+    }
+    B->group_first.push_back(B->count);
+}
+
+// One time step of instances [i0, i1) at the given parity; returns the parity after.
+cudaError_t one_step(cx_batch *B, int i0, int i1, int parity)
+{
+    const int w0 = B->work_begin[i0], w1 = B->work_begin[i1];
+    const int4 *work = B->d_work + w0;
+    cudaError_t e = cx::launch_batch_step(B->prec, B->law, B->mob, B->d_inst, work, w1 - w0,
+                                          parity, B->rows, 0, B->stream);
+    if (e == cudaSuccess && B->scheme == CX_SCHEME_HEUN)
+        e = cx::launch_batch_step(B->prec, B->law, B->mob, B->d_inst, work, w1 - w0, parity,
+                                  B->rows, 1, B->stream);
+    return e;
+}
+
+int next_parity(const cx_batch *B, int parity) { return B->scheme == CX_SCHEME_HEUN ? parity : parity ^ 1; }
+
+// Capture graph_steps steps of group gi starting at `parity` (an Euler chunk
+// is even, so it ends at the parity it started from).
+int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    BX_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    cudaError_t e = cudaSuccess;
+    int par = parity;
+    for (int s = 0; s < B->graph_steps && e == cudaSuccess; ++s) {
+        e = one_step(B, B->group_first[gi], B->group_first[gi + 1], par);
+        par = next_parity(B, par);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(B->stream, &graph);
+    if (e != cudaSuccess) return bcuda(e, "launch during graph capture");
+    if (e2 != cudaSuccess) return bcuda(e2, "graph capture end");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bcuda(e, "graph instantiate");
+    return CX_OK;
+}
+
+int check_batch(const cx_batch *B)
+{
+    if (!B) return bfail(CX_ERR_INVALID_ARG, "NULL batch");
+    return CX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params,
+                    const uint64_t *seeds, cx_batch **out)
+{
+    if (!out) return bfail(CX_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (count < 1 || count > 65535) return bfail(CX_ERR_INVALID_ARG, "count must lie in 1..65535");
+    if (!grids || !params || !seeds) return bfail(CX_ERR_INVALID_ARG, "grids, params and seeds must not be NULL");
+    for (int i = 0; i < count; ++i) {
+        int rc = cx::validate_params(&grids[i], &params[i]);
+        if (rc) return rc;
+        const cx_params &a = params[i], &z = params[0];
+        if (a.precision != z.precision || a.scheme != z.scheme || a.chemo_law != z.chemo_law ||
+            a.mobility != z.mobility || a.noise_mode != z.noise_mode)
+            return bfail(CX_ERR_INVALID_ARG, "all instances of a batch must share precision, "
+                                             "scheme, chemo_law, mobility and noise_mode");
+        if (a.noise_mode == CX_NOISE_PER_STEP)
+            return bfail(CX_ERR_UNSUPPORTED, "batches support static noise only");
+    }
+    cx_batch *B = new (std::nothrow) cx_batch;
+    if (!B) return bfail(CX_ERR_OOM, "host allocation of the batch failed");
+    B->count = count;
+    B->prec = params[0].precision;
+    B->law = params[0].chemo_law;
+    B->mob = params[0].mobility;
+    B->scheme = params[0].scheme;
+    B->elem = B->prec == CX_PREC_F64 ? sizeof(double) : sizeof(float);
+    B->g.assign(grids, grids + count);
+    B->p.assign(params, params + count);
+    B->seed.assign(seeds, seeds + count);
+    B->dt.resize(count);
+    for (int i = 0; i < count; ++i) {
+        int rc = cx::resolve_time_step(&grids[i], &params[i], &B->dt[i]);
+        if (rc) { free_batch(B); return rc; }
+    }
+    // arena layout
+    const long long align = 128 / (long long)B->elem;
+    std::vector<size_t> off(5 * (size_t)count);
+    size_t total = 0;
+    B->pitch.resize(count);
+    B->footprint.resize(count);
+    for (int i = 0; i < count; ++i) {
+        B->pitch[i] = ((long long)grids[i].nx + align - 1) / align * align;
+        const size_t bytes = round_up((size_t)B->pitch[i] * grids[i].ny * B->elem, 256);
+        for (int a = 0; a < 5; ++a) {
+            off[5 * i + a] = total;
+            total += bytes;
+        }
+        B->footprint[i] = (long long)(5 * bytes);
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { free_batch(B); return bcuda(e, "stream creation"); }
+    B->own_stream = true;
+    e = cudaMalloc(&B->arena, total);
+    if (e == cudaSuccess) e = cudaMemset(B->arena, 0, total);
+    if (e != cudaSuccess) { cudaGetLastError(); free_batch(B); return bcuda(e, "arena allocation"); }
+    for (int q = 0; q < 2; ++q) {
+        B->fb[q].resize(count);
+        B->fn[q].resize(count);
+    }
+    B->fs.resize(count);
+    char *base = (char *)B->arena;
+    for (int i = 0; i < count; ++i) {
+        B->fb[0][i] = base + off[5 * i + 0];
+        B->fb[1][i] = base + off[5 * i + 1];
+        B->fn[0][i] = base + off[5 * i + 2];
+        B->fn[1][i] = base + off[5 * i + 3];
+        B->fs[i] = base + off[5 * i + 4];
+    }
+    // instance table
+    const size_t isz = cx::inst_dev_bytes(B->prec);
+    B->h_inst.assign(isz * count, 0);
+    for (int i = 0; i < count; ++i)
+        cx::fill_inst(B->prec, B->h_inst.data(), i, B->fb[0][i], B->fb[1][i], B->fn[0][i],
+                      B->fn[1][i], B->fs[i], grids[i].nx, grids[i].ny, B->pitch[i],
+                      cx::make_coef(grids[i], params[i], B->dt[i]), cx::envelope_level(params[i]));
+    e = cudaMalloc(&B->d_inst, B->h_inst.size());
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_inst, B->h_inst.data(), B->h_inst.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_part, 8 * sizeof(double) * (size_t)count * kDiagBlocksPerInst);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_res, 8 * sizeof(double) * (size_t)count);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_res, 8 * sizeof(double) * (size_t)count);
+    if (e != cudaSuccess) { cudaGetLastError(); free_batch(B); return bcuda(e, "batch tables"); }
+    int rc = build_work(B);
+    if (rc) { free_batch(B); return rc; }
+    build_groups(B);
+    // initial state of every instance
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const cx_params &a = params[i];
+        e = cx::launch_sigma_init(B->prec, B->fs[i], grids[i].nx, grids[i].ny, B->pitch[i], seeds[i],
+                                  0, a.sigma0, a.noise_amp, a.noise_dist, 0, B->stream);
+        if (e == cudaSuccess)
+            e = cx::launch_initial_state(B->prec, B->fb[0][i], B->fn[0][i], grids[i].nx, grids[i].ny,
+                                         B->pitch[i], grids[i].dx, a.n0, a.bM, a.r0sq, B->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) { free_batch(B); return bcuda(e, "batch initialisation"); }
+    *out = B;
+    return CX_OK;
+}
+
+void cx_batch_destroy(cx_batch *B) { free_batch(B); }
+
+int cx_batch_set_stream(cx_batch *B, void *stream)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (!stream) return bfail(CX_ERR_INVALID_ARG, "a batch needs a non-default stream (graph capture)");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize old stream");
+    if (B->own_stream) cudaStreamDestroy(B->stream);
+    B->own_stream = false;
+    B->stream = (cudaStream_t)stream;
+    return CX_OK;
+}
+
+int cx_batch_set_tuning(cx_batch *B, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (tile_rows < 1 || tile_rows > 4096 || graph_steps < 0 || graph_steps > 100000 || group_bytes < 0)
+        return bfail(CX_ERR_INVALID_ARG, "tile_rows 1..4096, graph_steps 0..100000, group_bytes >= 0");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before retuning");
+    drop_graphs(B);
+    const bool new_rows = tile_rows != B->rows;
+    B->rows = tile_rows;
+    B->graph_steps = (B->scheme == CX_SCHEME_EULER && (graph_steps & 1)) ? graph_steps + 1 : graph_steps;
+    B->group_bytes = group_bytes;
+    if (new_rows) {
+        rc = build_work(B);
+        if (rc) return rc;
+    }
+    build_groups(B);
+    return CX_OK;
+}
+
+int cx_batch_get_tuning(cx_batch *B, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (tile_rows) *tile_rows = B->rows;
+    if (graph_steps) *graph_steps = B->graph_steps;
+    if (group_bytes) *group_bytes = B->group_bytes;
+    return CX_OK;
+}
+
+int cx_batch_step(cx_batch *B, int64_t n_steps)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (n_steps < 0) return bfail(CX_ERR_INVALID_ARG, "n_steps < 0");
+    if (n_steps == 0) return CX_OK;
+    const int ngroups = (int)B->group_first.size() - 1;
+    if (B->graph_steps > 0 && (int)B->gexec.size() != ngroups) {
+        drop_graphs(B);
+        B->gexec.assign(ngroups, nullptr);
+    }
+    int end_parity = B->cur;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int i0 = B->group_first[gi], i1 = B->group_first[gi + 1];
+        int par = B->cur;
+        int64_t left = n_steps;
+        if (B->graph_steps > 0 && left >= B->graph_steps) {
+            // Euler graphs start at parity 0 (and, being even, end there)
+            if (B->scheme == CX_SCHEME_EULER && par == 1) {
+                BX_CUDA(one_step(B, i0, i1, par), "batch step launch");
+                par = 0;
+                --left;
+            }
+            if (left >= B->graph_steps) {
+                if (!B->gexec[gi]) {
+                    rc = capture_group(B, gi, par, &B->gexec[gi]);
+                    if (rc) return rc;
+                }
+                while (left >= B->graph_steps) {
+                    BX_CUDA(cudaGraphLaunch(B->gexec[gi], B->stream), "graph launch");
+                    left -= B->graph_steps;
+                }
+            }
+        }
+        for (; left > 0; --left) {
+            BX_CUDA(one_step(B, i0, i1, par), "batch step launch");
+            par = next_parity(B, par);
+        }
+        end_parity = par;
+    }
+    B->cur = end_parity;
+    B->step += n_steps;
+    return CX_OK;
+}
+
+int cx_batch_synchronize(cx_batch *B)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    BX_CUDA(cudaStreamSynchronize(B->stream), "batch synchronize");
+    return CX_OK;
+}
+
+int cx_batch_diagnostics(cx_batch *B, cx_diag *out)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (!out) return bfail(CX_ERR_INVALID_ARG, "out must not be NULL");
+    BX_CUDA(cx::launch_batch_diag(B->prec, B->d_inst, 0, B->count, kDiagBlocksPerInst, B->cur,
+                                  B->d_part, B->d_res, B->stream),
+            "batch diagnostics launch");
+    BX_CUDA(cudaMemcpyAsync(B->h_res, B->d_res, 8 * sizeof(double) * (size_t)B->count,
+                            cudaMemcpyDeviceToHost, B->stream),
+            "batch diagnostics copy");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "batch diagnostics synchronize");
+    int worst = CX_OK;
+    for (int i = 0; i < B->count; ++i) {
+        const double *h = B->h_res + 8LL * i;
+        const double area = B->g[i].dx * B->g[i].dx;
+        cx_diag &d = out[i];
+        memset(&d, 0, sizeof d);
+        d.step = B->step;
+        d.dt = B->dt[i];
+        d.t = (double)B->step * B->dt[i];
+        d.mass_b = area * h[0];
+        d.mass_n = area * h[1];
+        d.invariant = area * (h[0] + B->p[i].theta * h[1]);
+        d.min_b = h[2];
+        d.min_n = h[3];
+        d.max_b = h[4];
+        d.r_env = h[5] >= 0.0 ? 0.5 * B->g[i].dx * sqrt(h[5]) : 0.0;
+        d.finite = h[6] == 0.0 ? 1 : 0;
+        d.status = !d.finite ? CX_ERR_NONFINITE
+                             : ((d.min_b < 0.0 || d.min_n < 0.0) ? CX_ERR_NEGATIVE : CX_OK);
+        if (d.status == CX_ERR_NONFINITE || (d.status != CX_OK && worst == CX_OK)) worst = d.status;
+    }
+    if (worst != CX_OK) return bfail(worst, "an instance of the batch is unhealthy (see status)");
+    return CX_OK;
+}
+
+static int batch_io(cx_batch *B, int32_t index, int32_t which, int32_t dtype, size_t count)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (index < 0 || index >= B->count) return bfail(CX_ERR_INVALID_ARG, "instance index out of range");
+    if (which < CX_FIELD_B || which > CX_FIELD_SIGMA) return bfail(CX_ERR_INVALID_ARG, "bad field");
+    if (dtype != CX_F64 && dtype != CX_F32) return bfail(CX_ERR_INVALID_ARG, "bad dtype");
+    if (count != (size_t)B->g[index].nx * (size_t)B->g[index].ny)
+        return bfail(CX_ERR_INVALID_ARG, "count != nx*ny of the instance");
+    return CX_OK;
+}
+
+static void *batch_field(cx_batch *B, int i, int which)
+{
+    if (which == CX_FIELD_B) return B->fb[B->cur][i];
+    if (which == CX_FIELD_N) return B->fn[B->cur][i];
+    return B->fs[i];
+}
+
+int cx_batch_get_field(cx_batch *B, int32_t index, int32_t which, void *host, int32_t dtype,
+                       size_t count)
+{
+    int rc = batch_io(B, index, which, dtype, count);
+    if (rc) return rc;
+    if (!host) return bfail(CX_ERR_INVALID_ARG, "host must not be NULL");
+    const int sd = B->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    const size_t row = (size_t)B->g[index].nx * B->elem;
+    std::vector<unsigned char> tmp;
+    void *dst = host;
+    if (dtype != sd) {
+        try { tmp.resize(count * B->elem); } catch (...) { return bfail(CX_ERR_OOM, "host staging"); }
+        dst = tmp.data();
+    }
+    BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before field read");
+    BX_CUDA(cudaMemcpy2DAsync(dst, row, batch_field(B, index, which), (size_t)B->pitch[index] * B->elem,
+                              row, B->g[index].ny, cudaMemcpyDeviceToHost, B->stream),
+            "field copy to host");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "field copy synchronize");
+    if (dtype != sd) {
+        if (sd == CX_F32)
+            for (size_t q = 0; q < count; ++q) ((double *)host)[q] = ((const float *)dst)[q];
+        else
+            for (size_t q = 0; q < count; ++q) ((float *)host)[q] = (float)((const double *)dst)[q];
+    }
+    return CX_OK;
+}
+
+int cx_batch_set_field(cx_batch *B, int32_t index, int32_t which, const void *host, int32_t dtype,
+                       size_t count)
+{
+    int rc = batch_io(B, index, which, dtype, count);
+    if (rc) return rc;
+    if (!host) return bfail(CX_ERR_INVALID_ARG, "host must not be NULL");
+    const int sd = B->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    const size_t row = (size_t)B->g[index].nx * B->elem;
+    std::vector<unsigned char> tmp;
+    const void *src = host;
+    if (dtype != sd) {
+        try { tmp.resize(count * B->elem); } catch (...) { return bfail(CX_ERR_OOM, "host staging"); }
+        if (sd == CX_F32)
+            for (size_t q = 0; q < count; ++q) ((float *)tmp.data())[q] = (float)((const double *)host)[q];
+        else
+            for (size_t q = 0; q < count; ++q) ((double *)tmp.data())[q] = ((const float *)host)[q];
+        src = tmp.data();
+    }
+    BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before field write");
+    BX_CUDA(cudaMemcpy2DAsync(batch_field(B, index, which), (size_t)B->pitch[index] * B->elem, src, row,
+                              row, B->g[index].ny, cudaMemcpyHostToDevice, B->stream),
+            "field copy to device");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "field copy synchronize");
+    return CX_OK;
+}
+
+int cx_batch_get_time(cx_batch *B, int32_t *count, int64_t *step)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (count) *count = B->count;
+    if (step) *step = B->step;
+    return CX_OK;
+}
+
+}  // extern "C"

@@ -47,6 +47,7 @@ struct StepArgs {
     int nx, ny;
     long long pitch;        // elements per row
     int law, mob, stage;
+    int rows;               // tile height in rows (grid.y = ceil(ny / rows))
     Coef k;
     Sigma sg;
     long long step;         // index of the time step being taken (noise counter)
@@ -74,6 +75,25 @@ cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, i
 // Store `msg` as this thread's cx_last_error() text; returns `code`.
 int record_error(int code, const char *msg);
 
+// Host helpers shared by the single-grid and batch entry points
+// (cx_api.cu): parameter validation, the time step (CX_ERR_DT_UNSTABLE
+// above the limit), the scaled flux coefficients and the envelope level.
+int validate_params(const cx_grid *g, const cx_params *p);
+int resolve_time_step(const cx_grid *g, const cx_params *p, double *dt);
+Coef make_coef(const cx_grid &g, const cx_params &p, double dt);
+double envelope_level(const cx_params &p);
+
+// Batched stepping and diagnostics (cx_batch.cu).  `inst` is the device
+// instance table, `work` the device work list (int4: instance, tile x,
+// tile y, unused).
+size_t inst_dev_bytes(int prec);
+void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void *n1, void *s,
+               int nx, int ny, long long pitch, const Coef &k, double bth);
+cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, const int4 *work,
+                              int nwork, int parity, int rows, int stage, cudaStream_t st);
+cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,
+                              int parity, double *part, double *out, cudaStream_t st);
+
 }  // namespace cx
 
 struct cx_ctx {
@@ -91,6 +111,7 @@ struct cx_ctx {
     cudaStream_t stream;
     int device;
     int time_block;
+    int tile_rows;        // rows per step-kernel tile
     cx::DiagScratch diag;
     double *h_diag;       // pinned [8]
 };

@@ -1,0 +1,199 @@
+// cx_reduce.cuh -- the diagnostics reduction shared by the single-grid and
+// batched diagnostics kernels: one record per thread / warp / block with
+// the sums of b and n, min b, min n, max b, the largest
+// (2i+1-nx)^2 + (2j+1-ny)^2 over cells with b >= b_th, and a non-finite flag.
+#pragma once
+
+#include <float.h>
+#include <stdint.h>
+
+#include "cx_internal.h"
+
+namespace cx {
+namespace reduce {
+
+constexpr int kThreads = 256;
+
+struct Acc {
+    double sb, sn;  // sums of b and n
+    double mnb, mnn, mxb;
+    long long r2;   // max (2i+1-nx)^2 + (2j+1-ny)^2 over b >= threshold, -1 if none
+    int bad;        // 1 if a non-finite cell was seen
+};
+
+__device__ __forceinline__ void combine(Acc &a, const Acc &o)
+{
+    a.sb += o.sb;
+    a.sn += o.sn;
+    a.mnb = fmin(a.mnb, o.mnb);
+    a.mnn = fmin(a.mnn, o.mnn);
+    a.mxb = fmax(a.mxb, o.mxb);
+    a.r2 = max(a.r2, o.r2);
+    a.bad |= o.bad;
+}
+
+__device__ __forceinline__ Acc shfl_down(const Acc &a, int d)
+{
+    Acc o;
+    o.sb = __shfl_down_sync(0xffffffffu, a.sb, d);
+    o.sn = __shfl_down_sync(0xffffffffu, a.sn, d);
+    o.mnb = __shfl_down_sync(0xffffffffu, a.mnb, d);
+    o.mnn = __shfl_down_sync(0xffffffffu, a.mnn, d);
+    o.mxb = __shfl_down_sync(0xffffffffu, a.mxb, d);
+    o.r2 = __shfl_down_sync(0xffffffffu, a.r2, d);
+    o.bad = __shfl_down_sync(0xffffffffu, a.bad, d);
+    return o;
+}
+
+__device__ __forceinline__ Acc empty_acc()
+{
+    Acc a;
+    a.sb = 0.0; a.sn = 0.0;
+    a.mnb = DBL_MAX; a.mnn = DBL_MAX; a.mxb = -DBL_MAX;
+    a.r2 = -1; a.bad = 0;
+    return a;
+}
+
+// Block-wide fold in a fixed order (blockDim.x == kThreads); the result is
+// valid in thread 0.
+__device__ __forceinline__ Acc block_reduce(Acc a)
+{
+    __shared__ Acc warp_acc[kThreads / 32];
+    for (int d = 16; d > 0; d >>= 1) combine(a, shfl_down(a, d));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) warp_acc[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = lane < kThreads / 32 ? warp_acc[lane] : empty_acc();
+        for (int d = 16; d > 0; d >>= 1) combine(a, shfl_down(a, d));
+    }
+    return a;
+}
+
+__device__ __forceinline__ void store_acc(double *dst, const Acc &a)
+{
+    dst[0] = a.sb; dst[1] = a.sn; dst[2] = a.mnb; dst[3] = a.mnn; dst[4] = a.mxb;
+    dst[5] = (double)a.r2;  // exact: below 2^53
+    dst[6] = (double)a.bad;
+    dst[7] = 0.0;
+}
+
+__device__ __forceinline__ Acc load_acc(const double *p)
+{
+    Acc o;
+    o.sb = p[0]; o.sn = p[1]; o.mnb = p[2]; o.mnn = p[3]; o.mxb = p[4];
+    o.r2 = (long long)p[5];
+    o.bad = (int)p[6];
+    return o;
+}
+
+// FP64 state: rows j = j0, j0 + jstep, ... of one grid, this thread's columns.
+__device__ __forceinline__ Acc rows_f64(const double *__restrict__ b, const double *__restrict__ n,
+                                        int nx, int ny, long long pitch, double bth, int j0,
+                                        int jstep)
+{
+    Acc a = empty_acc();
+    for (int j = j0; j < ny; j += jstep) {
+        const double *rb = b + (long long)j * pitch;
+        const double *rn = n + (long long)j * pitch;
+        const long long dy = 2LL * j + 1 - ny;
+        for (int i = threadIdx.x; i < nx; i += kThreads) {
+            const double vb = rb[i], vn = rn[i];
+            a.sb += vb;
+            a.sn += vn;
+            if (!isfinite(vb) || !isfinite(vn)) a.bad = 1;
+            a.mnb = fmin(a.mnb, vb);
+            a.mnn = fmin(a.mnn, vn);
+            a.mxb = fmax(a.mxb, vb);
+            if (vb >= bth) {
+                const long long ddx = 2LL * i + 1 - nx;
+                a.r2 = max(a.r2, ddx * ddx + dy * dy);
+            }
+        }
+    }
+    return a;
+}
+
+// Knuth's error-free sum: s + c += x with s, c in FP32; (s, c) keeps the
+// exact running total to O(len * eps^2).
+__device__ __forceinline__ void two_sum(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
+// FP32 state: GB300's FP64 pipe is far slower than its FP32 pipe, so each
+// thread sums its part of a row with compensated FP32 arithmetic and adds
+// the (sum, error) pair to its FP64 totals once per row.  Minima and maxima
+// are exact in FP32; `fth` is the least float f with (double)f >= b_th, so
+// the threshold test decides exactly as an FP64 comparison would.  The
+// envelope radius of a row is attained at its first or last column above
+// the threshold ((2i+1-nx)^2 is convex in i).  VEC: rows start 16-byte
+// aligned, so whole float4 vectors are read.
+template <bool VEC>
+__device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float *__restrict__ n,
+                                        int nx, int ny, long long pitch, float fth, int j0,
+                                        int jstep)
+{
+    double sb = 0.0, sn = 0.0;
+    float mnb = FLT_MAX, mnn = FLT_MAX, mxb = -FLT_MAX;
+    long long r2 = -1;
+    int bad = 0;
+    for (int j = j0; j < ny; j += jstep) {
+        const float *rb = b + (long long)j * pitch;
+        const float *rn = n + (long long)j * pitch;
+        float bs = 0.f, bc = 0.f, ns = 0.f, nc = 0.f;
+        int imin = 0x7fffffff, imax = -1;
+        auto cell = [&](int i, float vb, float vn) {
+            two_sum(bs, bc, vb);
+            two_sum(ns, nc, vn);
+            mnb = fminf(mnb, vb);
+            mnn = fminf(mnn, vn);
+            mxb = fmaxf(mxb, vb);
+            bad |= !(isfinite(vb) && isfinite(vn));
+            if (vb >= fth) {
+                imin = min(imin, i);
+                imax = max(imax, i);
+            }
+        };
+        int tail = 0;
+        if (VEC) {
+            const int nv = nx >> 2;
+            for (int v = threadIdx.x; v < nv; v += kThreads) {
+                const float4 qb = __ldg(reinterpret_cast<const float4 *>(rb) + v);
+                const float4 qn = __ldg(reinterpret_cast<const float4 *>(rn) + v);
+                cell(4 * v, qb.x, qn.x);
+                cell(4 * v + 1, qb.y, qn.y);
+                cell(4 * v + 2, qb.z, qn.z);
+                cell(4 * v + 3, qb.w, qn.w);
+            }
+            tail = nv << 2;
+        }
+        for (int i = tail + threadIdx.x; i < nx; i += kThreads) cell(i, rb[i], rn[i]);
+        sb += (double)bs + (double)bc;
+        sn += (double)ns + (double)nc;
+        if (imax >= 0) {
+            const long long d0 = 2LL * imin + 1 - nx, d1 = 2LL * imax + 1 - nx;
+            const long long dy = 2LL * j + 1 - ny;
+            r2 = max(r2, max(d0 * d0, d1 * d1) + dy * dy);
+        }
+    }
+    Acc a;
+    a.sb = sb; a.sn = sn;
+    a.mnb = (double)mnb; a.mnn = (double)mnn; a.mxb = (double)mxb;
+    a.r2 = r2; a.bad = bad;
+    return a;
+}
+
+// The least float f with (double)f >= t.
+inline float float_threshold(double t)
+{
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+}  // namespace reduce
+}  // namespace cx

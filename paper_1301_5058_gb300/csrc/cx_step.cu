@@ -4,7 +4,8 @@
 //
 // One pass per forward-Euler step reads b, n, sigma and writes b', n'
 // (20 B per cell in FP32, 40 B in FP64).  Each thread owns 4 adjacent cells
-// of a row (one 16-byte vector per FP32 field) and marches down kRows rows,
+// of a row (one 16-byte vector per FP32 field) and marches down one tile of
+// `rows` rows (32 by default; a tuning knob),
 // keeping the row ahead in registers, so every cell is loaded from HBM once
 // and every y-face flux is evaluated once and reused by the two cells that
 // share it.  x-neighbours come from the adjacent lanes by warp shuffles;
@@ -20,263 +21,12 @@
 //   STAGE 1  Heun's second stage u_out = (u0 + u* + dt r(u*)) / 2, reading
 //            u0 pointwise and overwriting it in place (second-order
 //            Runge-Kutta, Sec. 3)
-#include "cx_internal.h"
-#include "cx_philox.cuh"
+#include "cx_stencil.cuh"
 
 namespace cx {
 namespace {
 
-constexpr int kThreads = 128;  // 4 warps side by side along x
-constexpr int kCells = 4;      // cells per thread along x
-constexpr int kRows = 32;      // rows per block along y
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T> struct Vec;
-template <> struct Vec<float> {
-    // read-only path: for arrays no thread writes during the launch
-    static __device__ __forceinline__ void load(const float *p, float (&v)[4])
-    {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-    // coherent path: for the array the Heun combine overwrites in place
-    static __device__ __forceinline__ void load_rw(const float *p, float (&v)[4])
-    {
-        const float4 q = *reinterpret_cast<const float4 *>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-    static __device__ __forceinline__ void store(float *p, const float (&v)[4])
-    {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
-template <> struct Vec<double> {
-    static __device__ __forceinline__ void load(const double *p, double (&v)[4])
-    {
-        const double2 q0 = __ldg(reinterpret_cast<const double2 *>(p));
-        const double2 q1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
-    }
-    static __device__ __forceinline__ void load_rw(const double *p, double (&v)[4])
-    {
-        const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
-        const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
-        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
-    }
-    static __device__ __forceinline__ void store(double *p, const double (&v)[4])
-    {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-    }
-};
-
-// c / q for the receptor-law weight; FP32 uses the fast reciprocal (the FP32
-// path is judged by tolerance), FP64 the IEEE division.
-__device__ __forceinline__ float div_w(float c, float q) { return __fdividef(c, q); }
-__device__ __forceinline__ double div_w(double c, double q) { return c / q; }
-
-template <typename T> struct CoefT {
-    T cA, cChi, cG, cR, cN;
-};
-
-// Per-step noise: the sigma recipe of the state's precision.
-template <typename T> struct NoiseT;
-template <> struct NoiseT<float> {
-    uint64_t seed, step;
-    int dist;
-    float sigma0, amp;
-    __device__ __forceinline__ float at(long long idx) const
-    {
-        return sigma_f32(seed, (uint64_t)idx, step, dist, sigma0, amp);
-    }
-};
-template <> struct NoiseT<double> {
-    uint64_t seed, step;
-    int dist;
-    double sigma0, amp;
-    __device__ __forceinline__ double at(long long idx) const
-    {
-        return sigma_f64(seed, (uint64_t)idx, step, dist, sigma0, amp);
-    }
-};
-
-// Scaled fluxes (phi, g) through the face between L (left/lower) and R.
-template <typename T, int LAW, int MOB>
-__device__ __forceinline__ void face(T sL, T sR, T nL, T nR, T bL, T bR, const CoefT<T> &k,
-                                     T &phi, T &g)
-{
-    const T s2 = sL + sR, n2 = nL + nR, b2 = bL + bR;
-    const T db = bR - bL, dn = nR - nL;
-    T hc = k.cChi;  // chi(n_f) / 2
-    if (LAW == CX_CHEMO_RECEPTOR) {
-        const T q = T(2) + n2;
-        hc = div_w(k.cChi, q * q);
-    }
-    const T a = k.cA * s2 * n2;
-    if (MOB == CX_MOBILITY_CENTRAL) {
-        phi = a * b2 * (db - hc * b2 * dn);
-    } else {
-        const T bd = (dn >= T(0)) ? bL : bR;  // donor: the lower-n side
-        phi = a * (b2 * db - T(4) * hc * bd * bd * dn);
-    }
-    g = k.cG * dn;
-}
-
-template <typename T> struct Row {
-    T b[kCells], n[kCells], s[kCells];
-    T hb, hn, hs;              // lane 0: cell x0-1; lane 31: cell x0+4
-    T ub[kCells], un[kCells];  // STAGE 1: the state at the start of the step
-};
-
-template <typename T> struct Ptrs {
-    const T *__restrict__ b;
-    const T *__restrict__ n;
-    const T *__restrict__ s;
-    const T *bu;  // may alias bo (in-place Heun combine)
-    const T *nu;
-    T *bo;
-    T *no;
-};
-
-// One thread's march over rows j0..jend-1 in direction DIR (+1: increasing j,
-// -1: decreasing j).  The y-face shared with the row processed before
-// ("behind") is carried in registers; the y-face with the next row in march
-// order ("ahead") is computed from the row loaded in this iteration.  Face
-// values do not depend on DIR (a face is always evaluated with L the lower
-// row), so both directions give bit-identical results.
-template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR>
-__device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long long pitch,
-                                      const CoefT<T> &k, const NoiseT<T> &nz, int x0, int j0,
-                                      int jend)
-{
-    const int lane = threadIdx.x & 31;
-    // threads past the right edge keep running (they take part in the
-    // shuffles) but load an in-row vector and store nothing
-    const long long xv = min((long long)x0, pitch - kCells);
-    const bool halo_l = (lane == 0) && (x0 > 0) && (x0 < nx);
-    const bool halo_r = (lane == 31) && (x0 + kCells < nx);
-    const bool halo = halo_l || halo_r;
-    const long long xh = halo_l ? (long long)x0 - 1 : (long long)x0 + kCells;
-
-    auto load_row = [&](int r, Row<T> &R, bool own) {
-        const long long off = (long long)r * pitch;
-        Vec<T>::load(P.b + off + xv, R.b);
-        Vec<T>::load(P.n + off + xv, R.n);
-        if (NOISE == 0) {
-            Vec<T>::load(P.s + off + xv, R.s);
-        } else {
-            const long long row0 = (long long)r * nx;
-#pragma unroll
-            for (int c = 0; c < kCells; ++c)
-                R.s[c] = (x0 + c < nx) ? nz.at(row0 + x0 + c) : T(0);
-        }
-        R.hb = R.hn = R.hs = T(0);
-        if (halo) {
-            R.hb = __ldg(P.b + off + xh);
-            R.hn = __ldg(P.n + off + xh);
-            R.hs = NOISE == 0 ? __ldg(P.s + off + xh) : nz.at((long long)r * nx + xh);
-        }
-        if (STAGE == 1 && own) {
-            Vec<T>::load_rw(P.bu + off + xv, R.ub);
-            Vec<T>::load_rw(P.nu + off + xv, R.un);
-        }
-    };
-    // y-face between a lower row lo and an upper row hi
-    auto yface = [&](const Row<T> &lo, const Row<T> &hi, T (&ph)[kCells], T (&g)[kCells]) {
-#pragma unroll
-        for (int c = 0; c < kCells; ++c)
-            face<T, LAW, MOB>(lo.s[c], hi.s[c], lo.n[c], hi.n[c], lo.b[c], hi.b[c], k, ph[c], g[c]);
-    };
-
-    const int jfirst = DIR > 0 ? j0 : jend - 1;
-    const int jbehind = jfirst - DIR;
-    Row<T> cur, nxt;
-    T phB[kCells], gB[kCells];
-    load_row(jfirst, cur, true);
-    if (jbehind >= 0 && jbehind < ny) {
-        Row<T> prv;
-        load_row(jbehind, prv, false);
-        if (DIR > 0) yface(prv, cur, phB, gB);
-        else yface(cur, prv, phB, gB);
-    } else {
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) phB[c] = gB[c] = T(0);  // wall behind
-    }
-
-    const int rows = jend - j0;
-    for (int it = 0; it < rows; ++it) {
-        const int j = jfirst + DIR * it;
-        const int ja = j + DIR;
-        const bool has_a = (ja >= 0 && ja < ny);  // uniform across the block
-        if (has_a) load_row(ja, nxt, it + 1 < rows);
-
-        // x-neighbours of this thread's 4 cells
-        T lb = __shfl_up_sync(kFull, cur.b[kCells - 1], 1);
-        T ln = __shfl_up_sync(kFull, cur.n[kCells - 1], 1);
-        T ls = __shfl_up_sync(kFull, cur.s[kCells - 1], 1);
-        T rb = __shfl_down_sync(kFull, cur.b[0], 1);
-        T rn = __shfl_down_sync(kFull, cur.n[0], 1);
-        T rs = __shfl_down_sync(kFull, cur.s[0], 1);
-        if (lane == 0) { lb = cur.hb; ln = cur.hn; ls = cur.hs; }
-        if (lane == 31) { rb = cur.hb; rn = cur.hn; rs = cur.hs; }
-
-        // x-faces: f[c] lies between cells x0+c-1 and x0+c
-        T phX[kCells + 1], gX[kCells + 1];
-        face<T, LAW, MOB>(ls, cur.s[0], ln, cur.n[0], lb, cur.b[0], k, phX[0], gX[0]);
-#pragma unroll
-        for (int c = 1; c < kCells; ++c)
-            face<T, LAW, MOB>(cur.s[c - 1], cur.s[c], cur.n[c - 1], cur.n[c], cur.b[c - 1],
-                              cur.b[c], k, phX[c], gX[c]);
-        face<T, LAW, MOB>(cur.s[kCells - 1], rs, cur.n[kCells - 1], rn, cur.b[kCells - 1], rb, k,
-                          phX[kCells], gX[kCells]);
-        if (x0 == 0) phX[0] = gX[0] = T(0);  // west wall
-#pragma unroll
-        for (int c = 1; c <= kCells; ++c)
-            if (x0 + c >= nx) phX[c] = gX[c] = T(0);  // east wall (and padding)
-
-        // y-face with the row ahead (a wall past the grid's first/last row)
-        T phA[kCells], gA[kCells];
-        if (has_a) {
-            if (DIR > 0) yface(cur, nxt, phA, gA);
-            else yface(nxt, cur, phA, gA);
-        } else {
-#pragma unroll
-            for (int c = 0; c < kCells; ++c) phA[c] = gA[c] = T(0);
-        }
-
-        T ob[kCells], on[kCells];
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) {
-            const T phN = DIR > 0 ? phA[c] : phB[c], phS = DIR > 0 ? phB[c] : phA[c];
-            const T gN = DIR > 0 ? gA[c] : gB[c], gS = DIR > 0 ? gB[c] : gA[c];
-            const T r = cur.n[c] * cur.b[c];
-            const T divb = (phX[c + 1] - phX[c]) + (phN - phS);
-            const T divn = (gX[c + 1] - gX[c]) + (gN - gS);
-            ob[c] = (cur.b[c] + divb) + k.cR * r;
-            on[c] = (cur.n[c] + divn) - k.cN * r;
-            if (STAGE == 1) {
-                ob[c] = T(0.5) * (cur.ub[c] + ob[c]);
-                on[c] = T(0.5) * (cur.un[c] + on[c]);
-            }
-        }
-        const long long off = (long long)j * pitch;
-        if (x0 + kCells <= nx) {
-            Vec<T>::store(P.bo + off + x0, ob);
-            Vec<T>::store(P.no + off + x0, on);
-        } else {
-#pragma unroll
-            for (int c = 0; c < kCells; ++c)
-                if (x0 + c < nx) {
-                    P.bo[off + x0 + c] = ob[c];
-                    P.no[off + x0 + c] = on[c];
-                }
-        }
-
-        cur = nxt;
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) { phB[c] = phA[c]; gB[c] = gA[c]; }
-    }
-}
+using namespace stencil;
 
 // Row-bands alternate their march direction, so a halo row shared by two
 // neighbouring bands is read by both near the start (or both near the end)
@@ -284,11 +34,11 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
 // of one band and again at the end of the other.
 template <typename T, int LAW, int MOB, int NOISE, int STAGE>
 __global__ void __launch_bounds__(kThreads)
-    step_kernel(Ptrs<T> P, int nx, int ny, long long pitch, CoefT<T> k, NoiseT<T> nz)
+    step_kernel(Ptrs<T> P, int nx, int ny, long long pitch, CoefT<T> k, NoiseT<T> nz, int rows)
 {
     const int x0 = (blockIdx.x * kThreads + threadIdx.x) * kCells;
-    const int j0 = blockIdx.y * kRows;
-    const int jend = min(j0 + kRows, ny);
+    const int j0 = blockIdx.y * rows;
+    const int jend = min(j0 + rows, ny);
     if (blockIdx.y & 1)
         march<T, LAW, MOB, NOISE, STAGE, -1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
     else
@@ -308,8 +58,9 @@ cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
     Ptrs<T> P{(const T *)a.b, (const T *)a.n, (const T *)a.s, (const T *)a.bu,
               (const T *)a.nu, (T *)a.bo, (T *)a.no};
     const dim3 grid((a.nx + kThreads * kCells - 1) / (kThreads * kCells),
-                    (a.ny + kRows - 1) / kRows);
-    step_kernel<T, LAW, MOB, NOISE, STAGE><<<grid, kThreads, 0, st>>>(P, a.nx, a.ny, a.pitch, k, nz);
+                    (a.ny + a.rows - 1) / a.rows);
+    step_kernel<T, LAW, MOB, NOISE, STAGE><<<grid, kThreads, 0, st>>>(P, a.nx, a.ny, a.pitch, k, nz,
+                                                                        a.rows);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,22 @@ def perturbed_fields(nx: int, ny: int, seed: int, b_level=0.3, n_level=0.6, amp=
     return b.astype(np.float64), n.astype(np.float64)
 
 
+SWEEP_SIDES = (512, 1024, 1536, 2048)
+
+
+def sweep_specs(count: int = 512, seed: int = 0, precision: int = 1, steps: int = 20000):
+    """Batched sweep: `count` instances with sides drawn uniformly from
+    512..2048, (n0, chi0, sigma0) from sweep_points, instance seeds
+    0..count-1, static uniform noise a = 0.5, inoculum bM = 0.71 with
+    r0^2 = 32^2, FP32 state, dt = 0.2 x limit."""
+    rng = np.random.default_rng(seed + 1)
+    sides = rng.choice(SWEEP_SIDES, size=count)
+    n0, chi0, sigma0 = sweep_points(count, seed)
+    return [dict(nx=int(s), ny=int(s), dx=1.0, seed=i, n0=float(n0[i]), chi0=float(chi0[i]),
+                 sigma0=float(sigma0[i]), noise_amp=0.5, bM=0.71, r0sq=32.0 ** 2,
+                 precision=precision) for i, s in enumerate(sides)]
+
+
 def sweep_points(count: int, seed: int):
     """(n0, chi0, sigma0) on the log-spaced sweep box n0 in [0.1, 1.5],
     chi0 in {0} u [0.05, 4], sigma0 in [1, 8], drawn with a seeded generator."""

@@ -142,3 +142,30 @@ def test_load_rejects_missing_and_foreign_files(cx, tmp_path):
 def test_binding_refuses_non_float_host_arrays(cx):
     with pytest.raises(TypeError):
         cx._host_view(np.zeros(4, np.int32))
+
+
+def test_batch_create_validates_before_any_device_call(cx):
+    g = [cx.cx_grid(16, 16, 1.0), cx.cx_grid(8, 8, 1.0)]
+    p32 = cx.cx_params_default()
+    p64 = cx.cx_params_default(precision=cx.CX_PREC_F64)
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_batch_create(g, [p32, p64], [0, 1])
+    assert e.value.code == cx.CX_ERR_INVALID_ARG
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_batch_create(g, [p32, cx.cx_params_default(noise_amp=2.0)], [0, 1])
+    assert e.value.code == cx.CX_ERR_INVALID_ARG
+    ps = cx.cx_params_default(noise_mode=cx.CX_NOISE_PER_STEP)
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_batch_create(g, [ps, ps], [0, 1])
+    assert e.value.code == cx.CX_ERR_UNSUPPORTED
+    bad = cx.cx_params_default(dt=10.0)
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_batch_create(g, [p32, bad], [0, 1])
+    assert e.value.code == cx.CX_ERR_DT_UNSTABLE
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_batch_create([], [], [])
+    assert e.value.code == cx.CX_ERR_INVALID_ARG
+    for f, args in ((cx.lib().cx_batch_step, (None, 1)), (cx.lib().cx_batch_synchronize, (None,)),
+                    (cx.lib().cx_batch_set_tuning, (None, 32, 0, 0))):
+        assert f(*args) == cx.CX_ERR_INVALID_ARG
+    cx.lib().cx_batch_destroy(None)

@@ -367,3 +367,29 @@ def test_fp32_noise_recipe_tracks_the_fp64_recipe(dist):
     m = d.size
     ks = np.max(np.maximum(np.arange(1, m + 1) / m - F, F - np.arange(m) / m))
     assert ks < 1.63 / math.sqrt(m) + 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Threshold speed c* of the travelling-front problem (Appendix)
+
+def test_threshold_speed_of_the_porous_fisher_equation():
+    # u_t = (u u_x)_x + u (1 - u) has a sharp front moving at exactly
+    # 1/sqrt(2) (Newman 1980; Aronson 1980); with g = 4 u (1 - u) the speed
+    # scales by sqrt(4).
+    assert speed.threshold_speed(lambda u: u, lambda u: u * (1 - u), 2.0, tol=1e-6) == \
+        pytest.approx(1 / math.sqrt(2), rel=1e-5)
+    assert speed.threshold_speed(lambda u: u, lambda u: 4 * u * (1 - u), 4.0, tol=1e-6) == \
+        pytest.approx(math.sqrt(2), rel=1e-5)
+
+
+def test_c_star_below_c_bar_and_increasing_in_chi0():
+    # Eq. threshold: c* <= cbar; Prop. 1 (ii): c*(chi0) >= c*(0)
+    n0, sigma0 = 0.71, 1.0
+    cs = []
+    for chi0 in (0.0, 2.5):
+        D = lambda u, c=chi0: sigma0 * n0 * n0 * u * (1 - u) * (1 + c * n0 * u)
+        g = lambda u: n0 * u * (1 - u)
+        cs.append(speed.threshold_speed(D, g, 1.01 * speed.c_bar(n0, chi0, sigma0), tol=1e-5))
+        assert cs[-1] < speed.c_bar(n0, chi0, sigma0)
+        assert speed.mm_bound(D, g, 20001) == pytest.approx(speed.c_bar(n0, chi0, sigma0), rel=1e-6)
+    assert cs[1] > cs[0]
