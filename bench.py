@@ -160,6 +160,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Cross-rank pieces (replicas: each rank runs an independent grid; only the
+# timing crosses ranks)
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank's replica: the workload's seed plus the rank, so the
+    replicas are independent draws of the same configuration."""
+    return int(base) + int(rank)
+
+
+def max_over_ranks(values, world):
+    """Element-wise maximum over ranks of a list of floats (the slowest rank
+    sets the time); identity when world == 1.  Uses the current process
+    group (NCCL tensors live on the GPU, gloo tensors on the CPU)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
 
 def run_ours(args, rank, world, local_rank):
     import ctypes
@@ -178,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
     params["scheme"] = cx.CX_SCHEME_EULER if args.scheme == "euler" else cx.CX_SCHEME_HEUN
     params["noise_mode"] = cx.CX_NOISE_STATIC if args.noise == "static" else cx.CX_NOISE_PER_STEP
     params["noise_dist"] = cx.CX_NOISE_UNIFORM if args.dist == "uniform" else cx.CX_NOISE_TRIANGULAR
-    seed = seed + rank
+    seed = replica_seed(seed, rank)
     sim = cx.Sim(grid["nx"], grid["ny"], grid["dx"], seed=seed, **params)
     stream = torch.cuda.current_stream(dev)
     cx.cx_set_stream(sim.h, stream.cuda_stream)
@@ -296,14 +318,7 @@ def main():
     r = run_ours(args, rank, world, local_rank)
 
     elapsed, e2e_s = r["elapsed"], (r["e2e"] or {}).get("seconds")
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([elapsed, e2e_s or 0.0, r["per_launch"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed, e2e_s, per_launch = (float(v) for v in t.tolist())
-    else:
-        per_launch = r["per_launch"]
+    elapsed, e2e_s, per_launch = max_over_ranks([elapsed, e2e_s or 0.0, r["per_launch"]], world)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist

@@ -194,11 +194,6 @@ int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt);
  * restart from given data. */
 int cx_set_step(cx_ctx *c, int64_t step);
 
-/* Number of time steps fused per launch (temporal blocking depth), 1..8.
- * The result is bit-identical for every k.  Default 1. */
-int cx_set_time_block(cx_ctx *c, int32_t k);
-int cx_get_time_block(cx_ctx *c, int32_t *k);
-
 /* Height in rows of one step-kernel tile (each CTA marches one tile of
  * 512 columns x rows), 1..4096 with ceil(ny/rows) <= 65535; a performance
  * knob that the autotuner sets.  The result is bit-identical for every
@@ -267,6 +262,53 @@ int cx_batch_get_time(cx_batch *b, int32_t *count, int64_t *step);
 
 /* Free the batch.  NULL is a no-op. */
 void cx_batch_destroy(cx_batch *b);
+
+/* ---- morphology labels ----------------------------------------------------
+ *
+ * b sampled at nsamples points of the circle of `radius` (physical units)
+ * about the domain centre, sample k at angle 2 pi k / nsamples, by bilinear
+ * interpolation of the cell-centred values (clamped at the walls), into
+ * host_out[0..nsamples).  The number of circular runs above the envelope
+ * level at radius 0.8 r_env is the colony's branch count (the paper reads
+ * branch numbers off its figures, Sec. 3).  Synchronous. */
+int cx_polar_profile(cx_ctx *c, double radius, int32_t nsamples, double *host_out);
+int cx_batch_polar_profile(cx_batch *b, int32_t index, double radius, int32_t nsamples,
+                           double *host_out);
+
+/* ---- surrogate network ----------------------------------------------------
+ *
+ * An MLP 4 -> 256 -> 256 -> 2 with tanh hidden units that maps a sweep point
+ * (normalised n0, chi0, sigma0, a) to normalised morphology labels
+ * (envelope velocity, branch count), trained on data the solver produces.
+ * The 256 x 256 layer runs on the tensor cores with bf16 operands and FP32
+ * accumulation; everything else is FP32.  Parameters are FP32, packed as
+ * W1 (256 x 4, row-major), b1 (256), W2 (256 x 256), b2 (256), W3 (2 x 256),
+ * b3 (2): CX_MLP_PARAMS floats.  Loss = sum (Y - T)^2 / (2 B).  The paper
+ * has no counterpart: the network only proposes and pre-screens sweep
+ * points; every reported label comes from the solver. */
+#define CX_MLP_PARAMS 67586
+typedef struct cx_mlp cx_mlp;
+
+/* Allocate a network for batches of up to max_batch rows (1..2^20); the
+ * parameters start at zero (set them with cx_mlp_set_params). */
+int cx_mlp_create(int32_t max_batch, cx_mlp **out);
+/* Set / read all parameters (count == CX_MLP_PARAMS); setting them also
+ * resets the optimiser state. */
+int cx_mlp_set_params(cx_mlp *m, const float *host, size_t count);
+int cx_mlp_get_params(cx_mlp *m, float *host, size_t count);
+/* y (batch x 2) = network(x (batch x 4)), host arrays.  Synchronous. */
+int cx_mlp_forward(cx_mlp *m, const float *x, int32_t batch, float *y);
+/* Loss and its gradient (CX_MLP_PARAMS floats, same packing) on one batch. */
+int cx_mlp_gradient(cx_mlp *m, const float *x, const float *t, int32_t batch, float *grad,
+                    double *loss);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) over
+ * minibatches of `batch` consecutive rows of the n-row set (x, t), taken
+ * cyclically (shuffle the rows beforehand).  loss_out (optional, `steps`
+ * doubles) receives each step's minibatch loss.  Synchronous. */
+int cx_mlp_train(cx_mlp *m, const float *x, const float *t, int32_t n, int32_t batch,
+                 int32_t steps, float lr, double *loss_out);
+/* Free the network.  NULL is a no-op. */
+void cx_mlp_destroy(cx_mlp *m);
 
 /* ---- diagnostics without any allocation --------------------------------- */
 

@@ -89,8 +89,6 @@ _SIGNATURES = {
     "cx_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "cx_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
-    "cx_set_time_block": (ctypes.c_int, [_P, ctypes.c_int32]),
-    "cx_get_time_block": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cx_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "cx_destroy": (None, [_P]),
@@ -114,6 +112,18 @@ _SIGNATURES = {
     "cx_batch_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int64)]),
     "cx_batch_destroy": (None, [_P]),
+    "cx_polar_profile": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _P]),
+    "cx_batch_polar_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                              _P]),
+    "cx_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P)]),
+    "cx_mlp_set_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "cx_mlp_get_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "cx_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "cx_mlp_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "cx_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_float, _P]),
+    "cx_mlp_destroy": (None, [_P]),
     "cx_diagnostics_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _P, _P,
@@ -241,16 +251,6 @@ def cx_set_step(h, step: int):
     _check(lib().cx_set_step(h, step))
 
 
-def cx_set_time_block(h, k: int):
-    _check(lib().cx_set_time_block(h, k))
-
-
-def cx_get_time_block(h) -> int:
-    k = ctypes.c_int32()
-    _check(lib().cx_get_time_block(h, ctypes.byref(k)))
-    return k.value
-
-
 def cx_set_tile_rows(h, rows: int):
     _check(lib().cx_set_tile_rows(h, rows))
 
@@ -325,6 +325,86 @@ def cx_batch_set_field(h, index: int, which: int, src: np.ndarray):
 def cx_batch_destroy(h):
     if h:
         lib().cx_batch_destroy(h)
+
+
+def cx_polar_profile(h, radius: float, nsamples: int) -> np.ndarray:
+    out = np.empty(nsamples, np.float64)
+    _check(lib().cx_polar_profile(h, radius, nsamples, out.ctypes.data))
+    return out
+
+
+def cx_batch_polar_profile(h, index: int, radius: float, nsamples: int) -> np.ndarray:
+    out = np.empty(nsamples, np.float64)
+    _check(lib().cx_batch_polar_profile(h, index, radius, nsamples, out.ctypes.data))
+    return out
+
+
+CX_MLP_PARAMS = 67586
+
+
+def _f32(a, cols):
+    a = np.ascontiguousarray(a, np.float32)
+    if a.ndim != 2 or a.shape[1] != cols:
+        raise ValueError(f"expected an (n, {cols}) array")
+    return a
+
+
+class Mlp:
+    """The surrogate network (include/cx.h, cx_mlp_*)."""
+
+    def __init__(self, max_batch: int, params=None):
+        h = _P()
+        _check(lib().cx_mlp_create(max_batch, ctypes.byref(h)))
+        self.h = h.value
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, np.float32)
+        _check(lib().cx_mlp_set_params(self.h, theta.ctypes.data, theta.size))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(CX_MLP_PARAMS, np.float32)
+        _check(lib().cx_mlp_get_params(self.h, out.ctypes.data, out.size))
+        return out
+
+    def forward(self, x) -> np.ndarray:
+        x = _f32(x, 4)
+        y = np.empty((x.shape[0], 2), np.float32)
+        _check(lib().cx_mlp_forward(self.h, x.ctypes.data, x.shape[0], y.ctypes.data))
+        return y
+
+    def gradient(self, x, t):
+        x, t = _f32(x, 4), _f32(t, 2)
+        g = np.empty(CX_MLP_PARAMS, np.float32)
+        loss = ctypes.c_double()
+        _check(lib().cx_mlp_gradient(self.h, x.ctypes.data, t.ctypes.data, x.shape[0],
+                                     g.ctypes.data, ctypes.byref(loss)))
+        return loss.value, g
+
+    def train(self, x, t, batch: int, steps: int, lr: float) -> np.ndarray:
+        x, t = _f32(x, 4), _f32(t, 2)
+        losses = np.empty(steps, np.float64)
+        _check(lib().cx_mlp_train(self.h, x.ctypes.data, t.ctypes.data, x.shape[0], batch, steps,
+                                  lr, losses.ctypes.data))
+        return losses
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cx_mlp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cx_save(h, path: str):

@@ -144,7 +144,6 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     const long long align = 128 / (long long)c->elem;  // rows start on 128-byte lines
     c->pitch = ((long long)g->nx + align - 1) / align * align;
     c->dt = dt;
-    c->time_block = 1;
     // default tile height: 32 rows, or fewer so that a small grid still
     // launches about four 512-column tiles per SM (152 SMs) instead of a
     // handful of long, latency-bound marches
@@ -495,6 +494,25 @@ int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size
     return CX_OK;
 }
 
+int cx_polar_profile(cx_ctx *c, double radius, int32_t nsamples, double *host_out)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!host_out || nsamples < 1 || nsamples > (1 << 24) || !(isfinite(radius) && radius >= 0.0))
+        return fail(CX_ERR_INVALID_ARG, "need host_out, 1 <= nsamples <= 2^24, radius >= 0");
+    double *d = nullptr;
+    CX_CUDA(cudaMalloc((void **)&d, sizeof(double) * (size_t)nsamples), "profile buffer");
+    cudaError_t e = cx::launch_polar(c->prec, c->b[c->cur], c->g.nx, c->g.ny, c->pitch, c->g.dx,
+                                     radius, nsamples, d, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, d, sizeof(double) * (size_t)nsamples, cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "polar profile");
+    return CX_OK;
+}
+
 int cx_get_config(cx_ctx *c, cx_grid *g, cx_params *p, uint64_t *seed)
 {
     int rc = check_ctx(c);
@@ -527,15 +545,6 @@ int cx_set_step(cx_ctx *c, int64_t step)
     return CX_OK;
 }
 
-int cx_set_time_block(cx_ctx *c, int32_t k)
-{
-    int rc = check_ctx(c);
-    if (rc) return rc;
-    if (k < 1 || k > 8) return fail(CX_ERR_INVALID_ARG, "time block %d outside 1..8", k);
-    c->time_block = k;
-    return CX_OK;
-}
-
 int cx_set_tile_rows(cx_ctx *c, int32_t rows)
 {
     int rc = check_ctx(c);
@@ -553,15 +562,6 @@ int cx_get_tile_rows(cx_ctx *c, int32_t *rows)
     if (rc) return rc;
     if (!rows) return fail(CX_ERR_INVALID_ARG, "rows must not be NULL");
     *rows = c->tile_rows;
-    return CX_OK;
-}
-
-int cx_get_time_block(cx_ctx *c, int32_t *k)
-{
-    int rc = check_ctx(c);
-    if (rc) return rc;
-    if (!k) return fail(CX_ERR_INVALID_ARG, "k must not be NULL");
-    *k = c->time_block;
     return CX_OK;
 }
 

@@ -475,6 +475,28 @@ int cx_batch_set_field(cx_batch *B, int32_t index, int32_t which, const void *ho
     return CX_OK;
 }
 
+int cx_batch_polar_profile(cx_batch *B, int32_t index, double radius, int32_t nsamples,
+                           double *host_out)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (index < 0 || index >= B->count) return bfail(CX_ERR_INVALID_ARG, "instance index out of range");
+    if (!host_out || nsamples < 1 || nsamples > (1 << 24) || !(isfinite(radius) && radius >= 0.0))
+        return bfail(CX_ERR_INVALID_ARG, "need host_out, 1 <= nsamples <= 2^24, radius >= 0");
+    double *d = nullptr;
+    BX_CUDA(cudaMalloc((void **)&d, sizeof(double) * (size_t)nsamples), "profile buffer");
+    const cx_grid &g = B->g[index];
+    cudaError_t e = cx::launch_polar(B->prec, B->fb[B->cur][index], g.nx, g.ny, B->pitch[index], g.dx,
+                                     radius, nsamples, d, B->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, d, sizeof(double) * (size_t)nsamples, cudaMemcpyDeviceToHost,
+                            B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return bcuda(e, "polar profile");
+    return CX_OK;
+}
+
 int cx_batch_get_time(cx_batch *B, int32_t *count, int64_t *step)
 {
     int rc = check_batch(B);

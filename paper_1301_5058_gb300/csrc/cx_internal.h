@@ -72,6 +72,10 @@ cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, i
                                long long pitch, double b_threshold, DiagScratch s,
                                cudaStream_t st);
 
+// b on a circle of `radius` about the domain centre, ns samples (cx_labels.cu).
+cudaError_t launch_polar(int prec, const void *b, int nx, int ny, long long pitch, double dx,
+                         double radius, int ns, double *out, cudaStream_t st);
+
 // Store `msg` as this thread's cx_last_error() text; returns `code`.
 int record_error(int code, const char *msg);
 
@@ -110,7 +114,6 @@ struct cx_ctx {
     double dt;
     cudaStream_t stream;
     int device;
-    int time_block;
     int tile_rows;        // rows per step-kernel tile
     cx::DiagScratch diag;
     double *h_diag;       // pinned [8]

@@ -1,0 +1,248 @@
+"""Learned surrogate of the morphology map and the active boundary sweep.
+
+The plain solver is the judge throughout: it produces every training label
+and verifies every point the network proposes.
+
+Labels of a sweep point (n0, chi0, sigma0, a), computed from one solver run
+(a batch instance, forward Euler, FP32 state, static noise):
+  * envelope velocity: FP64 least-squares slope of the envelope radius
+    r_env(t) over the second half of the run (the paper tracks the colony
+    envelope, Sec. 3, and bounds its speed, Sec. 4.1);
+  * branch count: circular runs of b >= b_th on the circle r = 0.8 r_env
+    (4096 bilinear samples, cx_batch_polar_profile).
+
+Surrogate: the MLP of include/cx.h (4 -> 256 -> 256 -> 2, tanh), inputs
+(log n0, chi0, log sigma0, a) mapped affinely from the sweep box to
+[-1, 1]; outputs standardised by the training-set mean and spread.
+
+Active sweep: each round draws a pool of candidates, scores them by how
+close the network puts them to a morphology boundary (a predicted branch
+count near a class boundary, or a steep predicted velocity), sends the best
+`per_round` of them to the solver in one batch, adds the verified labels
+and retrains.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import paper_1301_5058_gb300 as cx
+
+BOX = {"n0": (0.1, 1.5), "chi0": (0.0, 4.0), "sigma0": (1.0, 8.0), "a": (0.0, 1.0)}
+
+
+def encode(points) -> np.ndarray:
+    """(N, 4) array of (n0, chi0, sigma0, a) -> network inputs in [-1, 1]."""
+    p = np.asarray(points, np.float64)
+    ln0 = (np.log(p[:, 0]) - math.log(BOX["n0"][0])) / math.log(BOX["n0"][1] / BOX["n0"][0])
+    c = p[:, 1] / BOX["chi0"][1]
+    ls = np.log(p[:, 2]) / math.log(BOX["sigma0"][1])
+    a = p[:, 3]
+    return (2.0 * np.stack([ln0, c, ls, a], 1) - 1.0).astype(np.float32)
+
+
+def draw_points(count: int, seed: int, a_range=(0.5, 0.5)) -> np.ndarray:
+    """Uniform draws in (log n0, chi0, log sigma0) over the sweep box."""
+    rng = np.random.default_rng(seed)
+    n0 = np.exp(rng.uniform(*np.log(BOX["n0"]), count))
+    chi0 = rng.uniform(*BOX["chi0"], count)
+    s0 = np.exp(rng.uniform(*np.log(BOX["sigma0"]), count))
+    a = rng.uniform(*a_range, count)
+    return np.stack([n0, chi0, s0, a], 1)
+
+
+def count_runs(profile, level) -> int:
+    above = np.asarray(profile) >= level
+    if above.all() or not above.any():
+        return 0
+    return int((above & ~np.roll(above, 1)).sum())
+
+
+def lsq_slope(t, r) -> float:
+    t = np.asarray(t, np.float64)
+    r = np.asarray(r, np.float64)
+    tm, rm = t.mean(), r.mean()
+    den = ((t - tm) ** 2).sum()
+    return float(((t - tm) * (r - rm)).sum() / den) if den > 0 else float("nan")
+
+
+def solver_labels(points, side=256, steps=4000, samples=40, seed0=0, r0sq=64.0,
+                  nsamples=4096, tune=None):
+    """Run every point as one batch instance and return (velocity, branches)
+    arrays plus the per-instance diagnostics at the end."""
+    pts = np.asarray(points, np.float64)
+    specs = [dict(nx=side, ny=side, dx=1.0, seed=seed0 + i, n0=float(p[0]), chi0=float(p[1]),
+                  sigma0=float(p[2]), noise_amp=float(p[3]), bM=0.71, r0sq=r0sq,
+                  precision=cx.CX_PREC_F32) for i, p in enumerate(pts)]
+    every = max(1, steps // samples)
+    t_hist, r_hist = [], []
+    with cx.Batch(specs) as bt:
+        if tune is not None:
+            bt.tune(*tune)
+        for _ in range(samples):
+            bt.step(every)
+            d = bt.diagnostics(check=False)
+            t_hist.append([x["t"] for x in d])
+            r_hist.append([x["r_env"] for x in d])
+        last = d
+        branches = []
+        for i, x in enumerate(last):
+            lvl = 0.1 * specs[i]["n0"]   # the envelope level 0.1 theta n0 (theta = 1)
+            prof = cx.cx_batch_polar_profile(bt.h, i, 0.8 * x["r_env"], nsamples)
+            branches.append(count_runs(prof, lvl))
+    t_hist = np.asarray(t_hist)
+    r_hist = np.asarray(r_hist)
+    half = samples // 2
+    vel = np.array([lsq_slope(t_hist[half:, i], r_hist[half:, i]) for i in range(len(pts))])
+    return vel, np.asarray(branches, np.float64), last
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Glorot-uniform weights, zero biases, packed as include/cx.h says."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(fo, fi):
+        lim = math.sqrt(6.0 / (fi + fo))
+        return rng.uniform(-lim, lim, (fo, fi))
+
+    parts = [glorot(256, 4), np.zeros(256), glorot(256, 256), np.zeros(256), glorot(2, 256),
+             np.zeros(2)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+class Surrogate:
+    """Network + output scaling.  predict() returns labels in solver units."""
+
+    def __init__(self, seed=0, max_batch=8192):
+        self.net = cx.Mlp(max_batch, init_params(seed))
+        self.seed = seed
+        self.mean = np.zeros(2)
+        self.scale = np.ones(2)
+
+    def fit(self, points, labels, steps=3000, lr=1e-3, batch=256, reinit=True):
+        X = encode(points)
+        Y = np.asarray(labels, np.float64)
+        self.mean = Y.mean(0)
+        self.scale = Y.std(0) + 1e-12
+        T = ((Y - self.mean) / self.scale).astype(np.float32)
+        rng = np.random.default_rng(self.seed + len(X))
+        perm = rng.permutation(len(X))
+        batch = min(batch, len(X))
+        if reinit:
+            self.net.set_params(init_params(self.seed))
+        return self.net.train(X[perm], T[perm], batch, steps, lr)
+
+    def predict(self, points) -> np.ndarray:
+        X = encode(points)
+        out = np.empty((len(X), 2))
+        for s in range(0, len(X), 8192):
+            out[s:s + 8192] = self.net.forward(X[s:s + 8192])
+        return out * self.scale + self.mean
+
+    def close(self):
+        self.net.close()
+
+
+def boundary_score(model: Surrogate, pts, level=1.5, eps=0.02):
+    """Higher = closer to a predicted morphology boundary: a branch count
+    near `level` or a steep predicted velocity (finite differences in the
+    normalised inputs)."""
+    pred = model.predict(pts)
+    near = -np.abs(pred[:, 1] - level)
+    X = encode(pts).astype(np.float64)
+    grad = np.zeros(len(pts))
+    for k in range(3):
+        step = np.zeros(4)
+        step[k] = eps
+        lo, hi = _decode(X - step), _decode(X + step)
+        d = (model.predict(hi)[:, 0] - model.predict(lo)[:, 0]) / (2 * eps)
+        grad += d * d
+    g = np.sqrt(grad)
+    gnorm = (g - g.mean()) / (g.std() + 1e-12)
+    nnorm = (near - near.mean()) / (near.std() + 1e-12)
+    return np.maximum(gnorm, nnorm)
+
+
+def _decode(X):
+    X = (np.asarray(X) + 1.0) / 2.0
+    n0 = BOX["n0"][0] * np.exp(X[:, 0] * math.log(BOX["n0"][1] / BOX["n0"][0]))
+    chi0 = X[:, 1] * BOX["chi0"][1]
+    s0 = np.exp(X[:, 2] * math.log(BOX["sigma0"][1]))
+    return np.stack([n0, chi0, s0, X[:, 3]], 1)
+
+
+def demo(side=256, steps=4000, n_train=256, n_test=128, train_steps=3000, seed=0):
+    """Label a training and a held-out set with the solver (one batch each),
+    train the network on the GPU, and report throughput and held-out error."""
+    import json
+    import time
+    out = {"side": side, "steps_per_point": steps}
+    t0 = time.perf_counter()
+    ptr = draw_points(n_train, seed, a_range=(0.0, 1.0))
+    vtr, btr, _ = solver_labels(ptr, side=side, steps=steps)
+    t1 = time.perf_counter()
+    pte = draw_points(n_test, seed + 99, a_range=(0.0, 1.0))
+    vte, bte, _ = solver_labels(pte, side=side, steps=steps, seed0=10_000)
+    out["solver_points_per_hour"] = n_train * 3600.0 / (t1 - t0)
+    out["branch_counts"] = {str(k): int(v) for k, v in zip(*np.unique(btr, return_counts=True))}
+    out["velocity_range"] = [float(vtr.min()), float(vtr.max())]
+    model = Surrogate(seed, max_batch=max(n_train, 1024))
+    t2 = time.perf_counter()
+    losses = model.fit(ptr, np.stack([vtr, btr], 1), steps=train_steps, lr=2e-3,
+                       batch=min(256, n_train))
+    t3 = time.perf_counter()
+    pred = model.predict(pte)
+    t4 = time.perf_counter()
+    big = draw_points(100_000, seed + 7)
+    t5 = time.perf_counter()
+    model.predict(big)
+    t6 = time.perf_counter()
+    rel = np.abs(pred[:, 0] - vte) / np.maximum(np.abs(vte), 1e-12)
+    out.update({
+        "train_seconds": t3 - t2, "final_loss": float(losses[-20:].mean()),
+        "heldout_velocity_rel_error_median": float(np.median(rel)),
+        "heldout_velocity_rel_error_p90": float(np.quantile(rel, 0.9)),
+        "heldout_within_1pct": float((rel <= 0.01).mean()),
+        "heldout_branch_abs_error_mean": float(np.mean(np.abs(pred[:, 1] - bte))),
+        "surrogate_points_per_hour": 100_000 * 3600.0 / (t6 - t5),
+    })
+    model.close()
+    print(json.dumps(out))
+    return out
+
+
+def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=None,
+                 train_kw=None):
+    """Surrogate-guided sweep.  Returns a dict with every verified point, its
+    labels, and per-round surrogate errors on the newly verified points."""
+    label_kw = label_kw or {}
+    train_kw = train_kw or {}
+    pts = draw_points(first, seed)
+    v, b, _ = solver_labels(pts, seed0=0, **label_kw)
+    P, L = pts, np.stack([v, b], 1)
+    model = Surrogate(seed)
+    history = []
+    for r in range(rounds):
+        model.fit(P, L, **train_kw)
+        cand = draw_points(pool, seed + 1000 + r)
+        score = boundary_score(model, cand)
+        pick = cand[np.argsort(-score)[:per_round]]
+        pred = model.predict(pick)
+        v, b, _ = solver_labels(pick, seed0=len(P), **label_kw)
+        rel = np.abs(pred[:, 0] - v) / np.maximum(np.abs(v), 1e-12)
+        history.append({"round": r, "median_rel_velocity_error": float(np.median(rel)),
+                        "mean_branch_error": float(np.mean(np.abs(pred[:, 1] - b)))})
+        P = np.concatenate([P, pick])
+        L = np.concatenate([L, np.stack([v, b], 1)])
+    model.close()
+    return {"points": P, "labels": L, "history": history}
+
+
+if __name__ == "__main__":
+    import sys
+    kw = {}
+    for a in sys.argv[1:]:
+        k, _, v = a.lstrip("-").partition("=")
+        kw[k] = int(v)
+    demo(**kw)

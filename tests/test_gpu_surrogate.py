@@ -1,0 +1,111 @@
+"""The learned part on the GPU: the network's forward pass and gradient
+against the FP64 oracle (with bf16 rounding at the same operands), training
+on the GPU, the polar-profile label against the oracle's bilinear sampling,
+and a small end-to-end surrogate fit on solver labels."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_1301_5058_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cx():
+    from paper_1301_5058_gb300 import _build
+    _build.build()
+    import paper_1301_5058_gb300 as cx
+    return cx
+
+
+def _theta(seed):
+    rng = np.random.default_rng(seed)
+    parts = {"W1": rng.normal(0, 0.5, (256, 4)), "b1": rng.normal(0, 0.1, 256),
+             "W2": rng.normal(0, 1 / 16, (256, 256)), "b2": rng.normal(0, 0.1, 256),
+             "W3": rng.normal(0, 1 / 16, (2, 256)), "b3": rng.normal(0, 0.1, 2)}
+    return omlp.pack(parts).astype(np.float32)
+
+
+def _blocks(v):
+    out, o = {}, 0
+    for name, shape in omlp.SHAPES:
+        k = int(np.prod(shape))
+        out[name] = np.asarray(v[o:o + k], np.float64)
+        o += k
+    return out
+
+
+@pytest.mark.parametrize("batch", [50, 128, 1000])
+def test_gradient_matches_oracle(cx, batch):
+    theta = _theta(batch)
+    rng = np.random.default_rng(batch + 1)
+    X = rng.uniform(-1, 1, (batch, 4)).astype(np.float32)
+    T = rng.normal(size=(batch, 2)).astype(np.float32)
+    with cx.Mlp(1024, theta) as net:
+        loss, g = net.gradient(X, T)
+        y = net.forward(X)
+    oloss, og = omlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64),
+                                   T.astype(np.float64), rounding=True)
+    oy, _ = omlp.forward(theta.astype(np.float64), X.astype(np.float64), rounding=True)
+    assert loss == pytest.approx(oloss, rel=1e-4)
+    assert np.linalg.norm(y - oy) <= 1e-4 * np.linalg.norm(oy)
+    gb, ob = _blocks(g), _blocks(og)
+    for name in gb:
+        err = np.linalg.norm(gb[name] - ob[name]) / max(np.linalg.norm(ob[name]), 1e-30)
+        assert err <= 1e-3, (name, err)
+
+
+def test_training_fits_a_smooth_map(cx):
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1, 1, (4096, 4)).astype(np.float32)
+    T = np.stack([np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2], np.cos(X[:, 3]) - X[:, 0] ** 2], 1)
+    T = T.astype(np.float32)
+    from paper_1301_5058_gb300 import surrogate
+    with cx.Mlp(4096, surrogate.init_params(1)) as net:
+        losses = net.train(X, T, 256, 3000, 2e-3)
+        y = net.forward(X)
+    assert losses[-20:].mean() < 0.02 * losses[:5].mean()
+    assert np.sqrt(((y - T) ** 2).mean()) < 0.05
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_polar_profile_matches_oracle(cx, prec):
+    cfg = dict(W.CONFIG0, nx=150, ny=120, chi0=1.0)
+    grid, params, seed = W.split(cfg)
+    with cx.Sim(150, 120, 0.7, seed=seed, **dict(params, precision=prec)) as sim:
+        sim.step(600)
+        b = sim.field(cx.CX_FIELD_B)
+        r = 0.8 * sim.diagnostics()["r_env"]
+        prof = cx.cx_polar_profile(sim.h, r, 4096)
+        edge = cx.cx_polar_profile(sim.h, 200.0, 256)   # far outside: clamped to the walls
+    ref = omlp.polar_profile(b, 0.7, r, 4096)
+    assert np.max(np.abs(prof - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
+    assert np.max(np.abs(edge - omlp.polar_profile(b, 0.7, 200.0, 256))) <= 1e-12
+
+
+def test_batch_polar_profile_matches_single(cx):
+    specs = [dict(nx=100, ny=90, dx=1.0, seed=3, n0=0.7, chi0=0.5, sigma0=4.0, noise_amp=0.5,
+                  bM=0.5, r0sq=16.0, precision=1)]
+    with cx.Batch(specs) as bt:
+        bt.step(300)
+        pb = cx.cx_batch_polar_profile(bt.h, 0, 9.5, 1000)
+        b = bt.field(0, cx.CX_FIELD_B)
+    assert np.max(np.abs(pb - omlp.polar_profile(b, 1.0, 9.5, 1000))) <= 1e-12
+
+
+def test_surrogate_end_to_end_small(cx):
+    from paper_1301_5058_gb300 import surrogate
+    pts = surrogate.draw_points(96, seed=5)
+    v, br, last = surrogate.solver_labels(pts, side=96, steps=800, samples=16)
+    assert np.all(np.isfinite(v)) and np.all(v >= 0)
+    assert all(d["finite"] == 1 for d in last)
+    model = surrogate.Surrogate(seed=2, max_batch=1024)
+    losses = model.fit(pts, np.stack([v, br], 1), steps=1500, lr=2e-3, batch=96)
+    pred = model.predict(pts)
+    model.close()
+    assert losses[-10:].mean() < 0.2 * losses[:5].mean()
+    # the fit explains most of the velocity variance on its training points
+    resid = ((pred[:, 0] - v) ** 2).mean() / max(v.var(), 1e-30)
+    assert resid < 0.2
