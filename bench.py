@@ -446,7 +446,8 @@ def main_sweep(args):
                                f"static uniform noise a=0.5, forward Euler, {args.point_steps} steps "
                                f"per point", "cells_per_time_step": cells,
                    "time_steps_per_step": S, "tuning": {"tile_rows": choice[0], "graph_steps": choice[1],
-                                                        "group_bytes": choice[2]}},
+                                                        "group_bytes": choice[2],
+                                                        "resident_steps": choice[3]}},
         "cell_updates_per_s": cells / per_step,
         "single_instance_points_per_hour": single_pph,
         "single_instance_ms_per_time_step": {str(k): v[0] * 1e3 for k, v in single.items()},

@@ -237,9 +237,19 @@ int cx_batch_set_stream(cx_batch *b, void *stream);
  *   group_bytes if > 0, instances are cut into consecutive groups whose
  *               fields fit this many bytes and each group runs all its steps
  *               before the next starts (keeps a group resident in L2);
- *               0: every launch covers every instance (default). */
-int cx_batch_set_tuning(cx_batch *b, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes);
-int cx_batch_get_tuning(cx_batch *b, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes);
+ *               0: every launch covers every instance (default);
+ *   resident_steps if > 0, each group advances up to this many steps per
+ *               launch: one cooperative launch whose resident blocks share
+ *               the group's tiles and meet at a grid barrier between steps
+ *               (the fields stay in L2 across steps); 0: one launch per step
+ *               (default).  Every barrier wait is bounded: if one runs out
+ *               (a fault, never in normal operation), the next
+ *               cx_batch_synchronize / cx_batch_diagnostics returns
+ *               CX_ERR_TIMEOUT and the batch state is undefined. */
+int cx_batch_set_tuning(cx_batch *b, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes,
+                        int32_t resident_steps);
+int cx_batch_get_tuning(cx_batch *b, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes,
+                        int32_t *resident_steps);
 
 /* Advance every instance by n_steps >= 0 steps.  Asynchronous. */
 int cx_batch_step(cx_batch *b, int64_t n_steps);

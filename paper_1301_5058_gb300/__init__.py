@@ -98,10 +98,12 @@ _SIGNATURES = {
                                        ctypes.POINTER(cx_params), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(_P)]),
     "cx_batch_set_stream": (ctypes.c_int, [_P, _P]),
-    "cx_batch_set_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]),
+    "cx_batch_set_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.c_int32]),
     "cx_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32),
-                                           ctypes.POINTER(ctypes.c_int64)]),
+                                           ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int32)]),
     "cx_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "cx_batch_synchronize": (ctypes.c_int, [_P]),
     "cx_batch_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(cx_diag)]),
@@ -277,14 +279,16 @@ def cx_batch_set_stream(h, stream: int):
     _check(lib().cx_batch_set_stream(h, stream))
 
 
-def cx_batch_set_tuning(h, tile_rows: int, graph_steps: int, group_bytes: int):
-    _check(lib().cx_batch_set_tuning(h, tile_rows, graph_steps, group_bytes))
+def cx_batch_set_tuning(h, tile_rows: int, graph_steps: int, group_bytes: int,
+                        resident_steps: int = 0):
+    _check(lib().cx_batch_set_tuning(h, tile_rows, graph_steps, group_bytes, resident_steps))
 
 
 def cx_batch_get_tuning(h):
-    r, g, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
-    _check(lib().cx_batch_get_tuning(h, ctypes.byref(r), ctypes.byref(g), ctypes.byref(b)))
-    return r.value, g.value, b.value
+    r, g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().cx_batch_get_tuning(h, ctypes.byref(r), ctypes.byref(g), ctypes.byref(b),
+                                     ctypes.byref(s)))
+    return r.value, g.value, b.value, s.value
 
 
 def cx_batch_step(h, n_steps: int):
@@ -515,8 +519,8 @@ class Batch:
     def set_field(self, index, which, arr):
         cx_batch_set_field(self.h, index, which, arr)
 
-    def tune(self, tile_rows, graph_steps, group_bytes):
-        cx_batch_set_tuning(self.h, tile_rows, graph_steps, group_bytes)
+    def tune(self, tile_rows, graph_steps, group_bytes, resident_steps=0):
+        cx_batch_set_tuning(self.h, tile_rows, graph_steps, group_bytes, resident_steps)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,8 +1,9 @@
 """Autotuner for the batched and single-grid steppers.
 
 The knobs change no result bit (include/cx.h): the tile height of the step
-kernel, the number of steps captured per CUDA graph, and the size of the
-instance groups a batch runs back to back (to keep a group resident in L2).
+kernel, the number of steps captured per CUDA graph, the size of the
+instance groups a batch runs back to back (to keep a group resident in L2),
+and how many steps a group advances per resident (cooperative) launch.
 Each candidate is timed with CUDA events on the handle's stream after a
 warm-up; the fastest is applied and cached in a JSON file keyed by
 precision, scheme and the mix of grid sizes (CX_TUNE_CACHE, default
@@ -18,10 +19,11 @@ import paper_1301_5058_gb300 as cx
 
 L2_BYTES = 126 * 2 ** 20   # GB300 L2 (about 126 MiB usable)
 
-BATCH_CANDIDATES = [(rows, graph, group)
-                    for rows in (8, 16, 32, 64)
-                    for graph in (0, 64)
-                    for group in (0, L2_BYTES // 2, L2_BYTES // 4)]
+# (tile rows, graph steps, group bytes, resident steps): one launch per step
+# over every instance, or L2-sized groups stepped by resident launches
+BATCH_CANDIDATES = ([(rows, graph, 0, 0) for rows in (8, 16, 32, 64) for graph in (0, 64)] +
+                    [(rows, 0, group, res) for rows in (4, 8, 16)
+                     for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)])
 SINGLE_CANDIDATES = (8, 16, 32, 64, 128)
 
 
@@ -95,8 +97,8 @@ def tune_batch(batch: "cx.Batch", steps: int = 128, reps: int = 3, candidates=No
         batch.step(steps)                      # warm-up (and graph capture)
         results[cand] = _time_steps(torch, stream, batch.step, steps, reps)
         if verbose:
-            print(f"  rows={cand[0]:3d} graph={cand[1]:3d} group={cand[2] >> 20:4d} MiB: "
-                  f"{results[cand] * 1e6:9.1f} us/step")
+            print(f"  rows={cand[0]:3d} graph={cand[1]:3d} group={cand[2] >> 20:4d} MiB "
+                  f"resident={cand[3]:4d}: {results[cand] * 1e6:9.1f} us/step")
     choice = min(results, key=results.get)
     batch.tune(*choice)
     _store(key, {"choice": list(choice), "us_per_step": results[choice] * 1e6})

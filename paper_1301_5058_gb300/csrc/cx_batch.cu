@@ -42,14 +42,13 @@ template <typename T> struct InstDev {
     double bth;    // FP64 envelope threshold
 };
 
+// One tile (work item w) of one step.
 // stage 0: u_out(parity^1) = u(parity) + dt r(u(parity))
 // stage 1: u(parity) = (u(parity) + u*(parity^1) + dt r(u*)) / 2, in place
-template <typename T, int LAW, int MOB, int STAGE>
-__global__ void __launch_bounds__(kThreads)
-    batch_step_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
-                      int parity, int rows)
+template <typename T, int LAW, int MOB, int STAGE, bool CG>
+__device__ __forceinline__ void tile_step(const InstDev<T> *__restrict__ inst, const int4 w,
+                                          int parity, int rows)
 {
-    const int4 w = work[blockIdx.x];
     const InstDev<T> &I = inst[w.x];
     const int nx = I.nx, ny = I.ny;
     const long long pitch = I.pitch;
@@ -67,9 +66,85 @@ __global__ void __launch_bounds__(kThreads)
     const int j0 = w.z * rows;
     const int jend = min(j0 + rows, ny);
     if (w.z & 1)
-        march<T, LAW, MOB, 0, STAGE, -1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        march<T, LAW, MOB, 0, STAGE, -1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
     else
-        march<T, LAW, MOB, 0, STAGE, +1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        march<T, LAW, MOB, 0, STAGE, +1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+}
+
+// Grid-wide barrier of a cooperative launch (every block is resident).  The
+// wait is bounded: after spin_limit polls the block records a failure and
+// leaves; a block that sees a recorded failure does not wait at all.
+// Returns false (in every thread of the block) on failure.
+struct GridBarrier {
+    unsigned count, gen;
+    int err, pad;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long spin_limit)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile GridBarrier *v = gb;
+        ok = v->err ? 0 : 1;
+        if (ok) {
+            const unsigned g = v->gen;
+            __threadfence();  // this block's writes before its arrival
+            const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+            if (arrived == gridDim.x) {
+                atomicExch(&gb->count, 0u);
+                __threadfence();
+                atomicAdd(&gb->gen, 1u);
+            } else {
+                long long it = 0;
+                while (v->gen == g) {
+                    if (++it > spin_limit) {
+                        atomicExch(&gb->err, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();  // the other blocks' writes before this block reads
+            if (v->err) ok = 0;
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Several steps of a group of instances in one cooperative launch: the
+// group's tiles are dealt to the resident blocks, and a grid barrier
+// separates the steps (and Heun's stages).  Loads go through L2 only.
+template <typename T, int LAW, int MOB, int HEUN>
+__global__ void __launch_bounds__(kThreads, 5)  // 96 registers, no spills
+    batch_resident_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
+                          int nwork, int parity, int rows, int nsteps, GridBarrier *gb,
+                          long long spin_limit)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        for (int w = blockIdx.x; w < nwork; w += gridDim.x)
+            tile_step<T, LAW, MOB, 0, true>(inst, work[w], parity, rows);
+        if (!grid_barrier(gb, spin_limit)) return;
+        if (HEUN) {
+            for (int w = blockIdx.x; w < nwork; w += gridDim.x)
+                tile_step<T, LAW, MOB, 1, true>(inst, work[w], parity, rows);
+            if (!grid_barrier(gb, spin_limit)) return;
+        } else {
+            parity ^= 1;
+        }
+    }
+}
+
+// stage 0: u_out(parity^1) = u(parity) + dt r(u(parity))
+// stage 1: u(parity) = (u(parity) + u*(parity^1) + dt r(u*)) / 2, in place
+template <typename T, int LAW, int MOB, int STAGE>
+__global__ void __launch_bounds__(kThreads)
+    batch_step_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
+                      int parity, int rows)
+{
+    tile_step<T, LAW, MOB, STAGE, false>(inst, work[blockIdx.x], parity, rows);
 }
 
 // Diagnostics: block (r, i) reduces rows r, r + B, ... of instance i.
@@ -130,7 +205,65 @@ cudaError_t launch_batch_prec(int law, int mob, const void *inst, const int4 *wo
                : launch_batch_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, stage, st);
 }
 
+// Cooperative launch of the resident kernel with as many blocks as can be
+// resident at once (at most one per tile), so every block reaches every
+// barrier.
+template <typename T, int LAW, int MOB, int HEUN>
+cudaError_t launch_resident_h(const void *inst, const int4 *work, int nwork, int parity, int rows,
+                              int nsteps, void *gb, long long spin, cudaStream_t st)
+{
+    if (nwork <= 0 || nsteps <= 0) return cudaSuccess;
+    const void *kern = (const void *)batch_resident_kernel<T, LAW, MOB, HEUN>;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_resident_kernel<T, LAW, MOB, HEUN>, kThreads, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int grid = per_sm * sms;
+    if (grid > nwork) grid = nwork;
+    if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const InstDev<T> *ip = (const InstDev<T> *)inst;
+    GridBarrier *gp = (GridBarrier *)gb;
+    void *args[] = {(void *)&ip, (void *)&work, (void *)&nwork, (void *)&parity, (void *)&rows,
+                    (void *)&nsteps, (void *)&gp, (void *)&spin};
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), args, 0, st);
+}
+
+template <typename T, int LAW, int MOB>
+cudaError_t launch_resident_t(const void *inst, const int4 *work, int nwork, int parity, int rows,
+                              int nsteps, int heun, void *gb, long long spin, cudaStream_t st)
+{
+    return heun ? launch_resident_h<T, LAW, MOB, 1>(inst, work, nwork, parity, rows, nsteps, gb, spin, st)
+                : launch_resident_h<T, LAW, MOB, 0>(inst, work, nwork, parity, rows, nsteps, gb, spin, st);
+}
+
+template <typename T>
+cudaError_t launch_resident_prec(int law, int mob, const void *inst, const int4 *work, int nwork,
+                                 int parity, int rows, int nsteps, int heun, void *gb, long long spin,
+                                 cudaStream_t st)
+{
+    if (law == CX_CHEMO_RECEPTOR)
+        return mob == CX_MOBILITY_CENTRAL
+                   ? launch_resident_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st)
+                   : launch_resident_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st);
+    return mob == CX_MOBILITY_CENTRAL
+               ? launch_resident_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st)
+               : launch_resident_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st);
+}
+
 }  // namespace
+
+size_t grid_barrier_bytes() { return sizeof(GridBarrier); }
+
+cudaError_t launch_batch_resident(int prec, int law, int mob, const void *inst, const int4 *work,
+                                  int nwork, int parity, int rows, int nsteps, int heun,
+                                  void *barrier, long long spin_limit, cudaStream_t st)
+{
+    return prec == CX_PREC_F64
+               ? launch_resident_prec<double>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, st)
+               : launch_resident_prec<float>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, st);
+}
 
 cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, const int4 *work,
                               int nwork, int parity, int rows, int stage, cudaStream_t st)

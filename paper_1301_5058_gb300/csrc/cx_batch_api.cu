@@ -54,6 +54,9 @@ struct cx_batch {
     long long group_bytes = 0;
     std::vector<int> group_first;  // instance index where each group starts (+ count)
     std::vector<cudaGraphExec_t> gexec;
+    int resident_steps = 0;         // > 0: steps per cooperative launch of a group
+    void *d_barrier = nullptr;      // grid barrier state of the resident kernel
+    long long spin_limit = 1 << 22; // polls before a barrier wait gives up
     int cur = 0;
     int64_t step = 0;
     cudaStream_t stream = nullptr;
@@ -81,6 +84,7 @@ void free_batch(cx_batch *B)
     if (B->d_part) cudaFree(B->d_part);
     if (B->d_res) cudaFree(B->d_res);
     if (B->h_res) cudaFreeHost(B->h_res);
+    if (B->d_barrier) cudaFree(B->d_barrier);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
     delete B;
 }
@@ -162,6 +166,40 @@ int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out)
 int check_batch(const cx_batch *B)
 {
     if (!B) return bfail(CX_ERR_INVALID_ARG, "NULL batch");
+    return CX_OK;
+}
+
+// After the stream has drained: did a resident launch's barrier wait run
+// out?  The flag is cleared once reported.
+int check_barrier(cx_batch *B)
+{
+    int err = 0;
+    BX_CUDA(cudaMemcpy(&err, (char *)B->d_barrier + 8, sizeof err, cudaMemcpyDeviceToHost),
+            "barrier flag read");
+    if (err) {
+        BX_CUDA(cudaMemset((char *)B->d_barrier + 8, 0, sizeof err), "barrier flag reset");
+        return bfail(CX_ERR_TIMEOUT, "a grid barrier wait of the resident batch kernel ran out; "
+                                     "the batch state is undefined");
+    }
+    return CX_OK;
+}
+
+// `left` steps of instances [i0, i1) by cooperative launches of
+// resident_steps steps each; returns the parity after them.
+int run_resident(cx_batch *B, int i0, int i1, int par, int64_t left, int *par_out)
+{
+    const int w0 = B->work_begin[i0], w1 = B->work_begin[i1];
+    while (left > 0) {
+        const int chunk = (int)(left < B->resident_steps ? left : B->resident_steps);
+        BX_CUDA(cudaMemsetAsync(B->d_barrier, 0, 8, B->stream), "barrier reset");
+        BX_CUDA(cx::launch_batch_resident(B->prec, B->law, B->mob, B->d_inst, B->d_work + w0, w1 - w0,
+                                          par, B->rows, chunk, B->scheme == CX_SCHEME_HEUN,
+                                          B->d_barrier, B->spin_limit, B->stream),
+                "resident batch launch");
+        if (B->scheme == CX_SCHEME_EULER && (chunk & 1)) par ^= 1;
+        left -= chunk;
+    }
+    *par_out = par;
     return CX_OK;
 }
 
@@ -249,7 +287,10 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
     if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_part, 8 * sizeof(double) * (size_t)count * kDiagBlocksPerInst);
     if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_res, 8 * sizeof(double) * (size_t)count);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_res, 8 * sizeof(double) * (size_t)count);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_barrier, cx::grid_barrier_bytes());
+    if (e == cudaSuccess) e = cudaMemset(B->d_barrier, 0, cx::grid_barrier_bytes());
     if (e != cudaSuccess) { cudaGetLastError(); free_batch(B); return bcuda(e, "batch tables"); }
+    if (const char *s = getenv("CX_BARRIER_SPIN_LIMIT")) B->spin_limit = atoll(s);
     int rc = build_work(B);
     if (rc) { free_batch(B); return rc; }
     build_groups(B);
@@ -282,18 +323,22 @@ int cx_batch_set_stream(cx_batch *B, void *stream)
     return CX_OK;
 }
 
-int cx_batch_set_tuning(cx_batch *B, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes)
+int cx_batch_set_tuning(cx_batch *B, int32_t tile_rows, int32_t graph_steps, int64_t group_bytes,
+                        int32_t resident_steps)
 {
     int rc = check_batch(B);
     if (rc) return rc;
-    if (tile_rows < 1 || tile_rows > 4096 || graph_steps < 0 || graph_steps > 100000 || group_bytes < 0)
-        return bfail(CX_ERR_INVALID_ARG, "tile_rows 1..4096, graph_steps 0..100000, group_bytes >= 0");
+    if (tile_rows < 1 || tile_rows > 4096 || graph_steps < 0 || graph_steps > 100000 ||
+        group_bytes < 0 || resident_steps < 0 || resident_steps > 1000000)
+        return bfail(CX_ERR_INVALID_ARG, "tile_rows 1..4096, graph_steps 0..100000, group_bytes >= 0, "
+                                         "resident_steps 0..1000000");
     BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before retuning");
     drop_graphs(B);
     const bool new_rows = tile_rows != B->rows;
     B->rows = tile_rows;
     B->graph_steps = (B->scheme == CX_SCHEME_EULER && (graph_steps & 1)) ? graph_steps + 1 : graph_steps;
     B->group_bytes = group_bytes;
+    B->resident_steps = resident_steps;
     if (new_rows) {
         rc = build_work(B);
         if (rc) return rc;
@@ -302,13 +347,15 @@ int cx_batch_set_tuning(cx_batch *B, int32_t tile_rows, int32_t graph_steps, int
     return CX_OK;
 }
 
-int cx_batch_get_tuning(cx_batch *B, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes)
+int cx_batch_get_tuning(cx_batch *B, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes,
+                        int32_t *resident_steps)
 {
     int rc = check_batch(B);
     if (rc) return rc;
     if (tile_rows) *tile_rows = B->rows;
     if (graph_steps) *graph_steps = B->graph_steps;
     if (group_bytes) *group_bytes = B->group_bytes;
+    if (resident_steps) *resident_steps = B->resident_steps;
     return CX_OK;
 }
 
@@ -328,6 +375,11 @@ int cx_batch_step(cx_batch *B, int64_t n_steps)
         const int i0 = B->group_first[gi], i1 = B->group_first[gi + 1];
         int par = B->cur;
         int64_t left = n_steps;
+        if (B->resident_steps > 0) {
+            rc = run_resident(B, i0, i1, par, left, &end_parity);
+            if (rc) return rc;
+            continue;
+        }
         if (B->graph_steps > 0 && left >= B->graph_steps) {
             // Euler graphs start at parity 0 (and, being even, end there)
             if (B->scheme == CX_SCHEME_EULER && par == 1) {
@@ -362,7 +414,7 @@ int cx_batch_synchronize(cx_batch *B)
     int rc = check_batch(B);
     if (rc) return rc;
     BX_CUDA(cudaStreamSynchronize(B->stream), "batch synchronize");
-    return CX_OK;
+    return check_barrier(B);
 }
 
 int cx_batch_diagnostics(cx_batch *B, cx_diag *out)
@@ -377,6 +429,8 @@ int cx_batch_diagnostics(cx_batch *B, cx_diag *out)
                             cudaMemcpyDeviceToHost, B->stream),
             "batch diagnostics copy");
     BX_CUDA(cudaStreamSynchronize(B->stream), "batch diagnostics synchronize");
+    rc = check_barrier(B);
+    if (rc) return rc;
     int worst = CX_OK;
     for (int i = 0; i < B->count; ++i) {
         const double *h = B->h_res + 8LL * i;

@@ -97,6 +97,14 @@ cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, cons
                               int nwork, int parity, int rows, int stage, cudaStream_t st);
 cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,
                               int parity, double *part, double *out, cudaStream_t st);
+// nsteps steps of the work items [0, nwork) in one cooperative launch with
+// a bounded grid barrier between steps; `barrier` is a device block of
+// grid_barrier_bytes() whose first 8 bytes must be zero at launch and whose
+// int at offset 8 becomes non-zero if a wait ran out.
+size_t grid_barrier_bytes();
+cudaError_t launch_batch_resident(int prec, int law, int mob, const void *inst, const int4 *work,
+                                  int nwork, int parity, int rows, int nsteps, int heun,
+                                  void *barrier, long long spin_limit, cudaStream_t st);
 
 }  // namespace cx
 

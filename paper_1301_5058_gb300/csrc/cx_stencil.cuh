@@ -28,6 +28,13 @@ template <> struct Vec<float> {
         const float4 q = *reinterpret_cast<const float4 *>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
+    // L2 path (bypasses L1): for a persistent launch, where the arrays a
+    // block reads were written by other blocks earlier in the same launch
+    static __device__ __forceinline__ void load_cg(const float *p, float (&v)[4])
+    {
+        const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
     static __device__ __forceinline__ void store(float *p, const float (&v)[4])
     {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -44,6 +51,12 @@ template <> struct Vec<double> {
     {
         const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
         const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+    static __device__ __forceinline__ void load_cg(const double *p, double (&v)[4])
+    {
+        const double2 q0 = __ldcg(reinterpret_cast<const double2 *>(p));
+        const double2 q1 = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
         v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
     }
     static __device__ __forceinline__ void store(double *p, const double (&v)[4])
@@ -126,8 +139,10 @@ template <typename T> struct Ptrs {
 // ("behind") is carried in registers; the y-face with the next row in march
 // order ("ahead") is computed from the row loaded in this iteration.  Face
 // values do not depend on DIR (a face is always evaluated with L the lower
-// row), so both directions give bit-identical results.
-template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR>
+// row), so both directions give bit-identical results.  CG: read through L2
+// only (a persistent launch whose blocks read what other blocks wrote
+// earlier in the same launch).
+template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR, bool CG = false>
 __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long long pitch,
                                       const CoefT<T> &k, const NoiseT<T> &nz, int x0, int j0,
                                       int jend)
@@ -141,12 +156,17 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
     const bool halo = halo_l || halo_r;
     const long long xh = halo_l ? (long long)x0 - 1 : (long long)x0 + kCells;
 
+    auto vload = [](const T *p, T (&v)[kCells]) {
+        if (CG) Vec<T>::load_cg(p, v);
+        else Vec<T>::load(p, v);
+    };
+    auto sload = [](const T *p) -> T { return CG ? __ldcg(p) : __ldg(p); };
     auto load_row = [&](int r, Row<T> &R, bool own) {
         const long long off = (long long)r * pitch;
-        Vec<T>::load(P.b + off + xv, R.b);
-        Vec<T>::load(P.n + off + xv, R.n);
+        vload(P.b + off + xv, R.b);
+        vload(P.n + off + xv, R.n);
         if (NOISE == 0) {
-            Vec<T>::load(P.s + off + xv, R.s);
+            vload(P.s + off + xv, R.s);
         } else {
             const long long row0 = (long long)r * nx;
 #pragma unroll
@@ -155,13 +175,18 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
         }
         R.hb = R.hn = R.hs = T(0);
         if (halo) {
-            R.hb = __ldg(P.b + off + xh);
-            R.hn = __ldg(P.n + off + xh);
-            R.hs = NOISE == 0 ? __ldg(P.s + off + xh) : nz.at((long long)r * nx + xh);
+            R.hb = sload(P.b + off + xh);
+            R.hn = sload(P.n + off + xh);
+            R.hs = NOISE == 0 ? sload(P.s + off + xh) : nz.at((long long)r * nx + xh);
         }
         if (STAGE == 1 && own) {
-            Vec<T>::load_rw(P.bu + off + xv, R.ub);
-            Vec<T>::load_rw(P.nu + off + xv, R.un);
+            if (CG) {
+                Vec<T>::load_cg(P.bu + off + xv, R.ub);
+                Vec<T>::load_cg(P.nu + off + xv, R.un);
+            } else {
+                Vec<T>::load_rw(P.bu + off + xv, R.ub);
+                Vec<T>::load_rw(P.nu + off + xv, R.un);
+            }
         }
     };
     // y-face between a lower row lo and an upper row hi

@@ -116,6 +116,7 @@ class Surrogate:
 
     def __init__(self, seed=0, max_batch=8192):
         self.net = cx.Mlp(max_batch, init_params(seed))
+        self.max_batch = max_batch
         self.seed = seed
         self.mean = np.zeros(2)
         self.scale = np.ones(2)
@@ -136,8 +137,9 @@ class Surrogate:
     def predict(self, points) -> np.ndarray:
         X = encode(points)
         out = np.empty((len(X), 2))
-        for s in range(0, len(X), 8192):
-            out[s:s + 8192] = self.net.forward(X[s:s + 8192])
+        c = self.max_batch
+        for s in range(0, len(X), c):
+            out[s:s + c] = self.net.forward(X[s:s + c])
         return out * self.scale + self.mean
 
     def close(self):

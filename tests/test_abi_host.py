@@ -166,6 +166,6 @@ def test_batch_create_validates_before_any_device_call(cx):
         cx.cx_batch_create([], [], [])
     assert e.value.code == cx.CX_ERR_INVALID_ARG
     for f, args in ((cx.lib().cx_batch_step, (None, 1)), (cx.lib().cx_batch_synchronize, (None,)),
-                    (cx.lib().cx_batch_set_tuning, (None, 32, 0, 0))):
+                    (cx.lib().cx_batch_set_tuning, (None, 32, 0, 0, 0))):
         assert f(*args) == cx.CX_ERR_INVALID_ARG
     cx.lib().cx_batch_destroy(None)

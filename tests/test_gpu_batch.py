@@ -45,7 +45,9 @@ def single_runs(cx, sp, steps, dtype):
 
 
 @pytest.mark.parametrize("prec,scheme", [(1, 0), (0, 0), (1, 1)])
-@pytest.mark.parametrize("tuning", [(32, 0, 0), (8, 10, 0), (64, 64, 0), (16, 12, 400_000)])
+@pytest.mark.parametrize("tuning", [(32, 0, 0, 0), (8, 10, 0, 0), (64, 64, 0, 0),
+                                    (16, 12, 400_000, 0), (8, 0, 400_000, 7), (4, 0, 0, 50),
+                                    (32, 0, 0, 1)])
 def test_batch_matches_single_grids_bitwise(cx, prec, scheme, tuning):
     sp = specs(prec, scheme)
     dtype = np.float32 if prec == 1 else np.float64
@@ -93,7 +95,29 @@ def test_batch_field_io_and_errors(cx):
             cx.cx_batch_get_field(bt.h, 0, cx.CX_FIELD_B, np.empty(5))
         with pytest.raises(cx.CxError):
             bt.tune(0, 1, 0)
+        with pytest.raises(cx.CxError):
+            bt.tune(8, 0, 0, -1)
         assert cx.cx_batch_get_time(bt.h) == (2, 0)
+
+
+def test_resident_barrier_timeout_is_reported(cx, monkeypatch):
+    # failure detection without a GPU fault: a spin limit of 0 makes every
+    # grid-barrier wait give up at once; the kernel returns, the context
+    # stays usable, and the host reports CX_ERR_TIMEOUT
+    monkeypatch.setenv("CX_BARRIER_SPIN_LIMIT", "0")
+    sp = specs(1, 0, sizes=[(600, 97), (513, 33), (130, 70)])
+    with cx.Batch(sp) as bt:
+        bt.tune(4, 0, 0, 20)
+        bt.step(40)
+        with pytest.raises(cx.CxError) as e:
+            cx.cx_batch_synchronize(bt.h)
+        assert e.value.code == cx.CX_ERR_TIMEOUT
+        cx.cx_batch_synchronize(bt.h)          # the flag was cleared
+    monkeypatch.delenv("CX_BARRIER_SPIN_LIMIT")
+    with cx.Batch(specs(1, 0, sizes=[(64, 48)])) as bt2:  # the device still works
+        bt2.tune(8, 0, 0, 10)
+        bt2.step(20)
+        assert bt2.diagnostics()[0]["finite"] == 1
 
 
 def test_single_grid_tile_rows_do_not_change_results(cx):
