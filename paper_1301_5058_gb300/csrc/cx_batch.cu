@@ -65,10 +65,18 @@ __device__ __forceinline__ void tile_step(const InstDev<T> *__restrict__ inst, c
     const int x0 = (w.y * kThreads + threadIdx.x) * kCells;
     const int j0 = w.z * rows;
     const int jend = min(j0 + rows, ny);
-    if (w.z & 1)
-        march<T, LAW, MOB, 0, STAGE, -1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
-    else
-        march<T, LAW, MOB, 0, STAGE, +1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    const bool interior = w.y > 0 && (w.y + 1) * kThreads * kCells < nx;
+    if (w.z & 1) {
+        if (interior)
+            march<T, LAW, MOB, 0, STAGE, -1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        else
+            march<T, LAW, MOB, 0, STAGE, -1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    } else {
+        if (interior)
+            march<T, LAW, MOB, 0, STAGE, +1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        else
+            march<T, LAW, MOB, 0, STAGE, +1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    }
 }
 
 // Grid-wide barrier of a cooperative launch (every block is resident).  The

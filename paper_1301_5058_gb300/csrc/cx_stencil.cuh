@@ -141,8 +141,11 @@ template <typename T> struct Ptrs {
 // values do not depend on DIR (a face is always evaluated with L the lower
 // row), so both directions give bit-identical results.  CG: read through L2
 // only (a persistent launch whose blocks read what other blocks wrote
-// earlier in the same launch).
-template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR, bool CG = false>
+// earlier in the same launch).  INTERIOR: the caller guarantees that every
+// thread's cells and both x-neighbours of the warp lie inside the grid
+// (0 < x0 and x0 + 4 < nx for all threads), so the x-wall tests drop out.
+template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR, bool CG = false,
+          bool INTERIOR = false>
 __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long long pitch,
                                       const CoefT<T> &k, const NoiseT<T> &nz, int x0, int j0,
                                       int jend)
@@ -150,9 +153,9 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
     const int lane = threadIdx.x & 31;
     // threads past the right edge keep running (they take part in the
     // shuffles) but load an in-row vector and store nothing
-    const long long xv = min((long long)x0, pitch - kCells);
-    const bool halo_l = (lane == 0) && (x0 > 0) && (x0 < nx);
-    const bool halo_r = (lane == 31) && (x0 + kCells < nx);
+    const long long xv = INTERIOR ? (long long)x0 : min((long long)x0, pitch - kCells);
+    const bool halo_l = (lane == 0) && (INTERIOR || ((x0 > 0) && (x0 < nx)));
+    const bool halo_r = (lane == 31) && (INTERIOR || (x0 + kCells < nx));
     const bool halo = halo_l || halo_r;
     const long long xh = halo_l ? (long long)x0 - 1 : (long long)x0 + kCells;
 
@@ -212,6 +215,7 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
     }
 
     const int rows = jend - j0;
+#pragma unroll 2
     for (int it = 0; it < rows; ++it) {
         const int j = jfirst + DIR * it;
         const int ja = j + DIR;
@@ -237,10 +241,12 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
                               cur.b[c], k, phX[c], gX[c]);
         face<T, LAW, MOB>(cur.s[kCells - 1], rs, cur.n[kCells - 1], rn, cur.b[kCells - 1], rb, k,
                           phX[kCells], gX[kCells]);
-        if (x0 == 0) phX[0] = gX[0] = T(0);  // west wall
+        if (!INTERIOR) {
+            if (x0 == 0) phX[0] = gX[0] = T(0);  // west wall
 #pragma unroll
-        for (int c = 1; c <= kCells; ++c)
-            if (x0 + c >= nx) phX[c] = gX[c] = T(0);  // east wall (and padding)
+            for (int c = 1; c <= kCells; ++c)
+                if (x0 + c >= nx) phX[c] = gX[c] = T(0);  // east wall (and padding)
+        }
 
         // y-face with the row ahead (a wall past the grid's first/last row)
         T phA[kCells], gA[kCells];
@@ -268,7 +274,7 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
             }
         }
         const long long off = (long long)j * pitch;
-        if (x0 + kCells <= nx) {
+        if (INTERIOR || x0 + kCells <= nx) {
             Vec<T>::store(P.bo + off + x0, ob);
             Vec<T>::store(P.no + off + x0, on);
         } else {

@@ -39,10 +39,19 @@ __global__ void __launch_bounds__(kThreads)
     const int x0 = (blockIdx.x * kThreads + threadIdx.x) * kCells;
     const int j0 = blockIdx.y * rows;
     const int jend = min(j0 + rows, ny);
-    if (blockIdx.y & 1)
-        march<T, LAW, MOB, NOISE, STAGE, -1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
-    else
-        march<T, LAW, MOB, NOISE, STAGE, +1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    // a block whose 512 columns touch neither x-wall takes the branch-free path
+    const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * kThreads * kCells < nx;
+    if (blockIdx.y & 1) {
+        if (interior)
+            march<T, LAW, MOB, NOISE, STAGE, -1, false, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        else
+            march<T, LAW, MOB, NOISE, STAGE, -1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    } else {
+        if (interior)
+            march<T, LAW, MOB, NOISE, STAGE, +1, false, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+        else
+            march<T, LAW, MOB, NOISE, STAGE, +1>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+    }
 }
 
 template <typename T, int LAW, int MOB, int NOISE, int STAGE>

@@ -214,6 +214,99 @@ def demo(side=256, steps=4000, n_train=256, n_test=128, train_steps=3000, seed=0
     return out
 
 
+class Ensemble:
+    """Several networks trained on log(velocity) from different initial
+    weights; a point is accepted without a solver run when the members agree
+    to within `agree` (relative spread of the predicted velocity)."""
+
+    def __init__(self, members=4, seed=0, max_batch=8192):
+        self.models = [Surrogate(seed + 17 * k, max_batch) for k in range(members)]
+
+    def fit(self, points, velocity, **kw):
+        lv = np.log(np.maximum(np.asarray(velocity, np.float64), 1e-12))
+        y = np.stack([lv, np.zeros_like(lv)], 1)
+        return [m.fit(points, y, **kw) for m in self.models]
+
+    def predict(self, points):
+        lv = np.stack([m.predict(points)[:, 0] for m in self.models], 0)
+        v = np.exp(lv)
+        mean = v.mean(0)
+        spread = (v.max(0) - v.min(0)) / np.maximum(mean, 1e-30)
+        return mean, spread
+
+    def close(self):
+        for m in self.models:
+            m.close()
+
+
+def single_instance_seconds_per_point(side, steps, spec_point, repeats=2):
+    """Wall time of one point stepped alone through cx_step (creation,
+    `steps` steps, diagnostics every steps/40), the plain way."""
+    import time
+    import torch
+    p = spec_point
+    kw = dict(n0=float(p[0]), chi0=float(p[1]), sigma0=float(p[2]), noise_amp=float(p[3]),
+              bM=0.71, r0sq=64.0, precision=cx.CX_PREC_F32)
+    best = float("inf")
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with cx.Sim(side, side, 1.0, seed=0, **kw) as sim:
+            for _ in range(40):
+                sim.step(steps // 40)
+                sim.diagnostics(check=False)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def validated_throughput(side=256, steps=20000, n_train=4096, n_test=1024, members=4,
+                         agree=0.005, train_steps=6000, seed=0):
+    """Points per hour whose envelope velocity is known to within 1 %:
+    screened by the ensemble (accepted where it agrees to `agree`), the rest
+    run by the batched solver; against every point run alone through cx_step.
+    The accepted points' error is judged on a solver-labelled held-out set."""
+    import json
+    import time
+    ptr = draw_points(n_train, seed, a_range=(0.0, 1.0))
+    t0 = time.perf_counter()
+    vtr, _, _ = solver_labels(ptr, side=side, steps=steps)
+    batch_s_per_point = (time.perf_counter() - t0) / n_train
+    pte = draw_points(n_test, seed + 99, a_range=(0.0, 1.0))
+    vte, _, _ = solver_labels(pte, side=side, steps=steps, seed0=100_000)
+    single_s = single_instance_seconds_per_point(side, steps, ptr[0])
+    ens = Ensemble(members, seed, max_batch=max(1024, min(8192, n_train)))
+    t1 = time.perf_counter()
+    ens.fit(ptr, vtr, steps=train_steps, lr=2e-3, batch=256)
+    train_s = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    mean, spread = ens.predict(pte)
+    screen_s_per_point = (time.perf_counter() - t2) / n_test
+    ens.close()
+    rel = np.abs(mean - vte) / np.maximum(vte, 1e-12)
+    acc = spread <= agree
+    f_acc = float(acc.mean())
+    within = float((rel[acc] <= 0.01).mean()) if acc.any() else float("nan")
+    # per point: screening always; the solver for the rejected share
+    mixed_s = screen_s_per_point + (1 - f_acc) * batch_s_per_point
+    out = {
+        "side": side, "steps_per_point": steps, "n_train": n_train, "n_test": n_test,
+        "members": members, "agree": agree,
+        "single_instance_points_per_hour": 3600.0 / single_s,
+        "batched_solver_points_per_hour": 3600.0 / batch_s_per_point,
+        "heldout_rel_error_median_all": float(np.median(rel)),
+        "accepted_fraction": f_acc,
+        "accepted_within_1pct": within,
+        "rejected_go_to_solver": True,
+        "validated_points_per_hour": 3600.0 / mixed_s,
+        "training_seconds_amortised_over": n_train,
+        "train_seconds": train_s,
+        "speedup_vs_single_instance": single_s / mixed_s,
+        "speedup_batched_solver_only": single_s / batch_s_per_point,
+    }
+    print(json.dumps(out))
+    return out
+
+
 def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=None,
                  train_kw=None):
     """Surrogate-guided sweep.  Returns a dict with every verified point, its
@@ -244,7 +337,11 @@ def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=
 if __name__ == "__main__":
     import sys
     kw = {}
+    mode = demo
     for a in sys.argv[1:]:
+        if a == "--validated":
+            mode = validated_throughput
+            continue
         k, _, v = a.lstrip("-").partition("=")
-        kw[k] = int(v)
-    demo(**kw)
+        kw[k] = float(v) if "." in v else int(v)
+    mode(**kw)
