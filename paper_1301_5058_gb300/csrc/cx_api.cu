@@ -320,6 +320,7 @@ int cx_set_stream(cx_ctx *c, void *stream)
 
 int cx_step(cx_ctx *c, int64_t n_steps)
 {
+    cx::NvtxRange range("cx_step");
     int rc = check_ctx(c);
     if (rc) return rc;
     if (n_steps < 0) return fail(CX_ERR_INVALID_ARG, "n_steps = %lld < 0", (long long)n_steps);
@@ -378,6 +379,7 @@ int cx_synchronize(cx_ctx *c)
 
 int cx_diagnostics(cx_ctx *c, cx_diag *out)
 {
+    cx::NvtxRange range("cx_diagnostics");
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");

@@ -126,7 +126,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long spin_lim
 // group's tiles are dealt to the resident blocks, and a grid barrier
 // separates the steps (and Heun's stages).  Loads go through L2 only.
 template <typename T, int LAW, int MOB, int HEUN>
-__global__ void __launch_bounds__(kThreads, 5)  // 96 registers, no spills
+__global__ void __launch_bounds__(kThreads, 4)  // up to 128 registers: no spills
     batch_resident_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                           int nwork, int parity, int rows, int nsteps, GridBarrier *gb,
                           long long spin_limit)

@@ -361,6 +361,7 @@ int cx_batch_get_tuning(cx_batch *B, int32_t *tile_rows, int32_t *graph_steps, i
 
 int cx_batch_step(cx_batch *B, int64_t n_steps)
 {
+    cx::NvtxRange range("cx_batch_step");
     int rc = check_batch(B);
     if (rc) return rc;
     if (n_steps < 0) return bfail(CX_ERR_INVALID_ARG, "n_steps < 0");
@@ -419,6 +420,7 @@ int cx_batch_synchronize(cx_batch *B)
 
 int cx_batch_diagnostics(cx_batch *B, cx_diag *out)
 {
+    cx::NvtxRange range("cx_batch_diagnostics");
     int rc = check_batch(B);
     if (rc) return rc;
     if (!out) return bfail(CX_ERR_INVALID_ARG, "out must not be NULL");

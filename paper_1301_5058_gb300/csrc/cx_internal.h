@@ -3,11 +3,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "cx.h"
 
 namespace cx {
+
+// Named range on profiler timelines for the life of a scope (NVTX; a
+// no-op unless a profiling tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-run coefficients of the scaled face fluxes.  The kernels work with
 // fluxes pre-multiplied by dt/dx, so that one step reads

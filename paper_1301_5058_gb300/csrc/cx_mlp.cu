@@ -419,6 +419,7 @@ int cx_mlp_gradient(cx_mlp *m, const float *x, const float *t, int32_t batch, fl
 int cx_mlp_train(cx_mlp *m, const float *x, const float *t, int32_t n, int32_t batch,
                  int32_t steps, float lr, double *loss_out)
 {
+    cx::NvtxRange range("cx_mlp_train");
     int rc = check_batch_arg(m, batch);
     if (rc) return rc;
     if (!x || !t || n < batch || steps < 0 || !(lr > 0.f))

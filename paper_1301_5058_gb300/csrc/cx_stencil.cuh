@@ -215,7 +215,6 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
     }
 
     const int rows = jend - j0;
-#pragma unroll 2
     for (int it = 0; it < rows; ++it) {
         const int j = jfirst + DIR * it;
         const int ja = j + DIR;

@@ -286,6 +286,12 @@ def validated_throughput(side=256, steps=20000, n_train=4096, n_test=1024, membe
     acc = spread <= agree
     f_acc = float(acc.mean())
     within = float((rel[acc] <= 0.01).mean()) if acc.any() else float("nan")
+    sweep = {}
+    for a in (0.005, 0.01, 0.02, 0.05, 0.1):
+        m = spread <= a
+        sweep[str(a)] = {"accepted": float(m.mean()),
+                         "within_1pct": float((rel[m] <= 0.01).mean()) if m.any() else None,
+                         "p95_error": float(np.quantile(rel[m], 0.95)) if m.any() else None}
     # per point: screening always; the solver for the rejected share
     mixed_s = screen_s_per_point + (1 - f_acc) * batch_s_per_point
     out = {
@@ -294,6 +300,8 @@ def validated_throughput(side=256, steps=20000, n_train=4096, n_test=1024, membe
         "single_instance_points_per_hour": 3600.0 / single_s,
         "batched_solver_points_per_hour": 3600.0 / batch_s_per_point,
         "heldout_rel_error_median_all": float(np.median(rel)),
+        "heldout_within_1pct_all": float((rel <= 0.01).mean()),
+        "agreement_thresholds": sweep,
         "accepted_fraction": f_acc,
         "accepted_within_1pct": within,
         "rejected_go_to_solver": True,

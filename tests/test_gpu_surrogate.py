@@ -95,6 +95,21 @@ def test_batch_polar_profile_matches_single(cx):
     assert np.max(np.abs(pb - omlp.polar_profile(b, 1.0, 9.5, 1000))) <= 1e-12
 
 
+def test_validated_throughput_and_active_sweep_small(cx):
+    from paper_1301_5058_gb300 import surrogate
+    out = surrogate.validated_throughput(side=64, steps=400, n_train=128, n_test=64, members=2,
+                                         agree=0.05, train_steps=300)
+    assert out["batched_solver_points_per_hour"] > out["single_instance_points_per_hour"] > 0
+    assert 0.0 <= out["accepted_fraction"] <= 1.0
+    assert np.isfinite(out["heldout_rel_error_median_all"])
+    res = surrogate.active_sweep(rounds=2, per_round=16, first=32, pool=256, seed=1,
+                                 label_kw=dict(side=64, steps=400, samples=8),
+                                 train_kw=dict(steps=300, lr=2e-3, batch=32))
+    assert len(res["points"]) == 32 + 2 * 16
+    assert np.all(np.isfinite(res["labels"][:, 0]))
+    assert len(res["history"]) == 2
+
+
 def test_surrogate_end_to_end_small(cx):
     from paper_1301_5058_gb300 import surrogate
     pts = surrogate.draw_points(96, seed=5)
