@@ -93,13 +93,14 @@ def step_kernel_traffic(prec):
     """ncu DRAM bytes per launch of the step kernel, if recorded for the
     current kernel source (null otherwise)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc", "cx_step.cu")
+    csrc = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != h:
+    digest = lambda name: hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != digest("cx_step.cu") or \
+            rec.get("stencil_sha256_16") != digest("cx_stencil.cuh"):
         return None
     return rec.get(prec, {}).get("dram_bytes_per_launch_16384sq")
 
