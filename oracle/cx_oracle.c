@@ -94,20 +94,25 @@ double orc_noise_delta(uint64_t seed, uint64_t idx, uint64_t step, int dist)
     return ldexp((double)num, -53);
 }
 
-/* FP32 recipe of the same draw, used when the state is held in FP32 and
- * sigma is redrawn every step: 24-bit integers j_a = w0 >> 8, j_b = w2 >> 8,
+/* FP32 recipe, used when the state is held in FP32 and sigma is redrawn
+ * every step: one Philox block serves the two cells of a pair, block
+ * counter (q lo, q hi, step lo, step hi) with q = idx >> 1, and cell idx
+ * takes words w[2h], w[2h+1] with h = idx & 1.  With the 24-bit integers
+ * j_a = w[2h] >> 8, j_b = w[2h+1] >> 8,
  *   dist 0:  Delta = (2 j_a - 2^24) 2^-24,   dist 1:  Delta = (j_a + j_b - 2^24) 2^-24,
  * exact in float, then sigma = sigma0 (1 + a Delta) with each float
  * operation rounded on its own. */
 float orc_noise_sigma_f32(uint64_t seed, uint64_t idx, uint64_t step, int dist,
                           float sigma0, float amp)
 {
-    uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32),
+    uint64_t q = idx >> 1;
+    int h = (int)(idx & 1);
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32),
                        (uint32_t)step, (uint32_t)(step >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
-    int32_t ja = (int32_t)(w[0] >> 8), jb = (int32_t)(w[2] >> 8);
+    int32_t ja = (int32_t)(w[2 * h] >> 8), jb = (int32_t)(w[2 * h + 1] >> 8);
     int32_t num = (dist == 0) ? (2 * ja - (1 << 24)) : (ja + jb - (1 << 24));
     float d = (float)num * 0x1p-24f;
     float t = amp * d;

@@ -85,6 +85,21 @@ template <> struct NoiseT<float> {
     {
         return sigma_f32(seed, (uint64_t)idx, step, dist, sigma0, amp);
     }
+    // cells idx0 .. idx0+3: two Philox blocks when idx0 is even, three when
+    // it is odd (the parity is the same for all threads of a row)
+    __device__ __forceinline__ void four(long long idx0, float (&s)[4]) const
+    {
+        const uint64_t q = (uint64_t)idx0 >> 1;
+        if ((idx0 & 1) == 0) {
+            sigma_pair_f32(seed, q, step, dist, sigma0, amp, s[0], s[1]);
+            sigma_pair_f32(seed, q + 1, step, dist, sigma0, amp, s[2], s[3]);
+        } else {
+            float unused0, unused1;
+            sigma_pair_f32(seed, q, step, dist, sigma0, amp, unused0, s[0]);
+            sigma_pair_f32(seed, q + 1, step, dist, sigma0, amp, s[1], s[2]);
+            sigma_pair_f32(seed, q + 2, step, dist, sigma0, amp, s[3], unused1);
+        }
+    }
 };
 template <> struct NoiseT<double> {
     uint64_t seed, step;
@@ -93,6 +108,11 @@ template <> struct NoiseT<double> {
     __device__ __forceinline__ double at(long long idx) const
     {
         return sigma_f64(seed, (uint64_t)idx, step, dist, sigma0, amp);
+    }
+    __device__ __forceinline__ void four(long long idx0, double (&s)[4]) const
+    {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[c] = at(idx0 + c);
     }
 };
 
@@ -171,10 +191,12 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
         if (NOISE == 0) {
             vload(P.s + off + xv, R.s);
         } else {
-            const long long row0 = (long long)r * nx;
+            nz.four((long long)r * nx + x0, R.s);
+            if (!INTERIOR) {
 #pragma unroll
-            for (int c = 0; c < kCells; ++c)
-                R.s[c] = (x0 + c < nx) ? nz.at(row0 + x0 + c) : T(0);
+                for (int c = 0; c < kCells; ++c)
+                    if (x0 + c >= nx) R.s[c] = T(0);  // past the row's end
+            }
         }
         R.hb = R.hn = R.hs = T(0);
         if (halo) {

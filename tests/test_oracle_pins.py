@@ -350,16 +350,27 @@ def test_c_bar_monotone_in_chi0():
 # FP32 recipe of the per-step noise
 
 @pytest.mark.parametrize("dist", [0, 1])
-def test_fp32_noise_recipe_tracks_the_fp64_recipe(dist):
-    # the 24-bit uniforms are the top bits of the 53-bit ones, so Delta moves
-    # by less than 2^-23, and three float roundings add at most 3 ulp
+def test_fp32_noise_recipe_laws_and_pairing(dist):
+    # the FP32 recipe draws a pair of cells from one Philox block: the values
+    # are exact floats, the law is uniform / triangular (KS), the two cells of
+    # a pair are uncorrelated, and a cell's value follows from the block of
+    # its pair (words 2h, 2h+1 of the known-answer-pinned generator)
     s0, a = 4.0, 0.8
-    s64 = oracle.sigma_field(300, 200, 11, s0, a, dist=dist, step=5)
     s32 = oracle.sigma_field_f32(300, 200, 11, s0, a, dist=dist, step=5)
-    assert np.all(s32 == s32.astype(np.float32))           # exactly float values
-    bound = s0 * (a * 2.0 ** -23 + 4 * 2.0 ** -24 * (1 + a))
-    assert np.max(np.abs(s32 - s64)) <= bound
-    d = np.sort(((s32 / s0 - 1) / a).ravel())
+    assert np.all(s32 == s32.astype(np.float32))
+    flat = ((s32 / s0 - 1) / a).ravel()
+    pairs = flat[: flat.size // 2 * 2].reshape(-1, 2)
+    rho = np.corrcoef(pairs[:, 0], pairs[:, 1])[0, 1]
+    assert abs(rho) < 5 / math.sqrt(len(pairs))
+    for idx in (0, 1, 12345, 59999):
+        w = oracle.philox4x32_10([idx >> 1, 0, 5, 0], [11, 0])
+        h = idx & 1
+        ja, jb = w[2 * h] >> 8, w[2 * h + 1] >> 8
+        num = 2 * ja - (1 << 24) if dist == 0 else ja + jb - (1 << 24)
+        d = np.float32(num) * np.float32(2.0 ** -24)
+        ref = np.float32(s0) * (np.float32(1.0) + np.float32(a) * d)
+        assert s32.ravel()[idx] == np.float64(ref)
+    d = np.sort(flat)
     if dist == 1:
         F = np.where(d <= 0, 0.5 * (1 + d) ** 2, 1 - 0.5 * (1 - d) ** 2)
     else:
