@@ -267,6 +267,59 @@ def test_field_io_converts_precision(cx):
 # the oracle checks one step on sampled windows (corners, edges, interior,
 # the ragged end of a block) from the same FP32 state.
 
+def _envelope_series(cx, cfg, prec, steps, samples):
+    with make_sim(cx, cfg, prec)[0] as sim:
+        d0 = sim.diagnostics()
+        t, r = [], []
+        for _ in range(samples):
+            sim.step(steps // samples)
+            d = sim.diagnostics()
+            t.append(d["t"])
+            r.append(d["r_env"])
+        gb = sim.field(cx.CX_FIELD_B)
+    return np.array(t), np.array(r), d0, d, gb
+
+
+def test_long_run_fp32_against_fp64_envelope(cx):
+    # beyond 1000 steps round-off is amplified by the growth of the colony, so
+    # long runs are compared on the envelope radius and its velocity (within
+    # 1 %) and on conservation; the FP64 GPU path is itself pinned to the
+    # oracle at 1e-12 (tests above)
+    cfg = dict(W.CONFIG1, nx=2048, ny=2048, r0sq=32.0 ** 2)
+    t64, r64, a64, z64, b64 = _envelope_series(cx, cfg, cx.CX_PREC_F64, 20000, 20)
+    t32, r32, a32, z32, b32 = _envelope_series(cx, cfg, cx.CX_PREC_F32, 20000, 20)
+    assert np.allclose(t32, t64, rtol=1e-12)
+    assert np.max(np.abs(r32 - r64) / r64) <= 0.01
+    h = len(t64) // 2
+    v64 = np.polyfit(t64[h:], r64[h:], 1)[0]
+    v32 = np.polyfit(t32[h:], r32[h:], 1)[0]
+    assert abs(v32 - v64) <= 0.01 * abs(v64)
+    assert abs(z64["invariant"] - a64["invariant"]) <= 1e-12 * a64["invariant"]
+    assert abs(z32["invariant"] - a32["invariant"]) <= 1e-5 * a32["invariant"]
+    print(f"\nFP32 vs FP64, 2048^2, 20000 steps: rel L2(b) = {rel_l2(b32, b64):.3e}, "
+          f"max rel r_env diff = {np.max(np.abs(r32 - r64) / r64):.3e}, v32 = {v32:.6f}, "
+          f"v64 = {v64:.6f}, FP32 invariant drift = "
+          f"{abs(z32['invariant'] - a32['invariant']) / a32['invariant']:.3e}")
+
+
+@pytest.mark.parametrize("n,steps", [(256, 100), (256, 1000), (1024, 1000)])
+def test_error_table_fp32_fp64_against_oracle(cx, n, steps):
+    # relative L2 error of both GPU precisions against the FP64 oracle
+    cfg = dict(W.CONFIG0, nx=n, ny=n)
+    s, b, n0 = oracle_inputs(cfg)
+    ob, on = oracle_run(cfg, s, b, n0, steps)
+    errs = {}
+    for prec in (cx.CX_PREC_F64, cx.CX_PREC_F32):
+        with make_sim(cx, cfg, prec)[0] as sim:
+            sim.set_field(cx.CX_FIELD_B, b)
+            sim.set_field(cx.CX_FIELD_N, n0)
+            sim.step(steps)
+            errs[prec] = (rel_l2(sim.field(cx.CX_FIELD_B), ob), rel_l2(sim.field(cx.CX_FIELD_N), on))
+    print(f"\n{n}^2 x {steps} steps: FP64 rel L2 (b, n) = {errs[0][0]:.2e}, {errs[0][1]:.2e}; "
+          f"FP32 = {errs[1][0]:.2e}, {errs[1][1]:.2e}")
+    assert max(errs[0]) <= TOL64 and max(errs[1]) <= TOL32
+
+
 def _window_error(cfg, dt, s, b0, n0, b1, n1, windows, size=40):
     nx, ny = cfg["nx"], cfg["ny"]
     worst = 0.0
