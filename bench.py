@@ -30,13 +30,24 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic HBM bytes per cell and time step: Euler reads b, n (and the
-# sigma array for static noise) and writes b', n'; Heun's second stage also
-# reads the start-of-step state pointwise
-def bytes_per_cell(prec, scheme, noise):
+# algorithmic HBM bytes per cell and time step.  One pass reads b, n (and
+# the sigma array for static noise) and writes b', n'.  Unfused, Euler takes
+# one pass per step and Heun two, the second also reading the start-of-step
+# state pointwise; fused (time block 2), one pass takes two Euler steps or a
+# whole Heun step.
+def bytes_per_cell(prec, scheme, noise, time_block=1):
     w = 4 if prec == "f32" else 8
-    euler = (5 if noise == "static" else 4) * w
-    return euler if scheme == "euler" else euler + euler + 2 * w
+    one_pass = (5 if noise == "static" else 4) * w
+    if time_block == 2:
+        return one_pass / 2 if scheme == "euler" else one_pass
+    return one_pass if scheme == "euler" else one_pass + one_pass + 2 * w
+
+
+# kernel launches of cx_step(S)
+def launches_per_window(scheme, time_block, S):
+    if time_block == 2:
+        return S // 2 + S % 2 if scheme == "euler" else S
+    return S if scheme == "euler" else 2 * S
 
 
 def parse():
@@ -52,6 +63,9 @@ def parse():
     ap.add_argument("--scheme", default="euler", choices=["euler", "heun"])
     ap.add_argument("--noise", default="static", choices=["static", "per-step"])
     ap.add_argument("--dist", default="uniform", choices=["uniform", "triangular"])
+    ap.add_argument("--time-block", type=int, default=None, choices=[1, 2],
+                    help="explicit stages per pass over the grid (temporal blocking depth); "
+                         "default: the library's (2 for FP32, 1 for FP64)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="grid", choices=["grid", "sweep"],
@@ -75,6 +89,7 @@ def config_block(args, cfg):
                         f"{'forward Euler' if args.scheme == 'euler' else 'Heun RK2'}, "
                         f"dt=0.2 x limit",
             "nx": cfg["nx"], "ny": cfg["ny"], "time_steps_per_step": args.window,
+            "time_block": args.time_block,
             "diagnostics_per_step": 1,
             "l2": "inputs larger than L2 (3 fields x 1 GiB read per time step); no flush",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
@@ -89,18 +104,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def step_kernel_traffic(prec):
-    """ncu DRAM bytes per launch of the step kernel, if recorded for the
-    current kernel source (null otherwise)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+def kernel_traffic(prec, name):
+    """ncu DRAM bytes per launch of kernel `name` ("step_kernel" or
+    "fused_kernel") on the 16384^2 workload, if recorded for the current
+    sources of that kernel (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     csrc = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    digest = lambda name: hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != digest("cx_step.cu") or \
-            rec.get("stencil_sha256_16") != digest("cx_stencil.cuh"):
+    for src, h in rec.get("sources_sha256_16", {}).items():
+        p = os.path.join(csrc, src)
+        if not os.path.exists(p) or hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] != h:
+            return None
+    if not rec.get("sources_sha256_16"):
         return None
     return rec.get(prec, {}).get("dram_bytes_per_launch_16384sq")
 
@@ -205,6 +223,9 @@ def run_ours(args, rank, world, local_rank):
     sim = cx.Sim(grid["nx"], grid["ny"], grid["dx"], seed=seed, **params)
     stream = torch.cuda.current_stream(dev)
     cx.cx_set_stream(sim.h, stream.cuda_stream)
+    if args.time_block is not None:
+        cx.cx_set_time_block(sim.h, args.time_block)
+    args.time_block = cx.cx_get_time_block(sim.h)
     cells = cfg["nx"] * cfg["ny"]
     K, Wm, S = args.steps, args.warmup, args.window
 
@@ -331,7 +352,9 @@ def main():
     units = cells * S * K * world
     value = units / elapsed
     peak, peak_kind = peaks()
-    bpc = bytes_per_cell(args.precision, args.scheme, args.noise)
+    bpc = bytes_per_cell(args.precision, args.scheme, args.noise, args.time_block)
+    lpw = launches_per_window(args.scheme, args.time_block, S)
+    kernel = "fused_kernel" if args.time_block == 2 else "step_kernel"
     achieved = bpc * cells / per_launch / 1e9
     out = {
         "metric": "grid-cell updates/s",
@@ -349,11 +372,17 @@ def main():
         "config": config_block(args, cfg),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "traffic": step_kernel_traffic(args.precision),
+                     "kernel": kernel,
+                     "traffic": kernel_traffic(args.precision, kernel),
                      "algorithmic_bytes_per_cell": bpc,
                      "kernel_ms_per_time_step": per_launch * 1e3,
-                     "launches_per_time_step": 1 if args.scheme == "euler" else 2},
-        "gpu_launches": K * (S * (1 if args.scheme == "euler" else 2) + 2),
+                     # the HBM-roofline rate of a one-step-per-pass stepper
+                     # (20 B per FP32 cell-update): temporal blocking may pass it
+                     "one_step_pass_roofline_cell_updates_per_s":
+                         peak * 1e9 / bytes_per_cell(args.precision, args.scheme, args.noise, 1),
+                     "kernel_cell_updates_per_s": cells / per_launch,
+                     "launches_per_time_step": lpw / S},
+        "gpu_launches": K * (lpw + 2),
         "clocks": r["clocks"],
         "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b", "min_n")},
     }

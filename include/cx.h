@@ -195,12 +195,26 @@ int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt);
 int cx_set_step(cx_ctx *c, int64_t step);
 
 /* Height in rows of one step-kernel tile (each CTA marches one tile of
- * 512 columns x rows), 1..4096 with ceil(ny/rows) <= 65535; a performance
+ * 512 columns x rows, 480 x rows with two stages per pass), 1..4096 with
+ * ceil(ny/rows) <= 65535, or 0 for the automatic height; a performance
  * knob that the autotuner sets.  The result is bit-identical for every
- * value.  Default: 32, or fewer on small grids so that about four tiles
- * per SM are launched. */
+ * value.  Automatic: 32 rows (64 with two stages per pass), or fewer on
+ * small grids so that about four tiles per SM are launched; cx_get_tile_rows
+ * reports the height in effect. */
 int cx_set_tile_rows(cx_ctx *c, int32_t rows);
 int cx_get_tile_rows(cx_ctx *c, int32_t *rows);
+
+/* Temporal blocking depth: the number of explicit stages of Eq. ka-chem-model
+ * that one pass over the grid takes, 1 or 2.  At 2, cx_step runs two
+ * forward-Euler steps per pass (an odd remainder takes a single pass), or
+ * both stages of a Heun step in one pass, the intermediate state held in
+ * registers; a pass then reads and writes the state once for two stages.
+ * The result is bit-identical for both values (the stages evaluate the same
+ * operations on the same operands) and the stability limit is that of one
+ * step.  A performance knob; default 2 for an FP32 state, 1 for FP64 (whose
+ * pass is bound by the FP64 pipe).  Errors: INVALID_ARG. */
+int cx_set_time_block(cx_ctx *c, int32_t stages);
+int cx_get_time_block(cx_ctx *c, int32_t *stages);
 
 /* Write / read a checkpoint: header (grid, params, seed, step, dt,
  * precision) and the raw b, n and sigma arrays.  A run resumed from a

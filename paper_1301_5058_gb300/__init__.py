@@ -94,6 +94,8 @@ _SIGNATURES = {
     "cx_destroy": (None, [_P]),
     "cx_set_tile_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cx_get_tile_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "cx_set_time_block": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cx_get_time_block": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cx_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(cx_grid),
                                        ctypes.POINTER(cx_params), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(_P)]),
@@ -260,6 +262,16 @@ def cx_set_tile_rows(h, rows: int):
 def cx_get_tile_rows(h) -> int:
     r = ctypes.c_int32()
     _check(lib().cx_get_tile_rows(h, ctypes.byref(r)))
+    return r.value
+
+
+def cx_set_time_block(h, stages: int):
+    _check(lib().cx_set_time_block(h, stages))
+
+
+def cx_get_time_block(h) -> int:
+    r = ctypes.c_int32()
+    _check(lib().cx_get_time_block(h, ctypes.byref(r)))
     return r.value
 
 

@@ -24,7 +24,7 @@ L2_BYTES = 126 * 2 ** 20   # GB300 L2 (about 126 MiB usable)
 BATCH_CANDIDATES = ([(rows, graph, 0, 0) for rows in (8, 16, 32, 64) for graph in (0, 64)] +
                     [(rows, 0, group, res) for rows in (4, 8, 16)
                      for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)])
-SINGLE_CANDIDATES = (8, 16, 32, 64, 128)
+SINGLE_CANDIDATES = (8, 16, 32, 64, 128, 256)
 
 
 def cache_path() -> str:
@@ -106,25 +106,30 @@ def tune_batch(batch: "cx.Batch", steps: int = 128, reps: int = 3, candidates=No
 
 
 def tune_single(sim: "cx.Sim", steps: int = 20, reps: int = 3, use_cache: bool = True):
-    """Pick the tile height of a single grid; returns (rows, timings)."""
+    """Pick the temporal blocking depth and tile height of a single grid;
+    applies the winner and returns ((time_block, rows), timings)."""
     import torch
     key = f"single/p{sim.params.precision}/s{sim.params.scheme}/n{sim.params.noise_mode}/" \
           f"{sim.grid.nx}x{sim.grid.ny}"
     if use_cache:
         hit = _load_cache().get(key)
-        if hit:
-            cx.cx_set_tile_rows(sim.h, hit["choice"])
-            return hit["choice"], {}
+        if hit and isinstance(hit.get("choice"), list):
+            cx.cx_set_time_block(sim.h, hit["choice"][0])
+            cx.cx_set_tile_rows(sim.h, hit["choice"][1])
+            return tuple(hit["choice"]), {}
     stream = torch.cuda.current_stream()
     cx.cx_set_stream(sim.h, stream.cuda_stream)
     results = {}
-    for rows in SINGLE_CANDIDATES:
-        if (sim.grid.ny + rows - 1) // rows > 65535:
-            continue
-        cx.cx_set_tile_rows(sim.h, rows)
-        sim.step(steps)
-        results[rows] = _time_steps(torch, stream, sim.step, steps, reps)
+    for depth in (1, 2):
+        cx.cx_set_time_block(sim.h, depth)
+        for rows in SINGLE_CANDIDATES:
+            if (sim.grid.ny + rows - 1) // rows > 65535:
+                continue
+            cx.cx_set_tile_rows(sim.h, rows)
+            sim.step(steps)
+            results[(depth, rows)] = _time_steps(torch, stream, sim.step, steps, reps)
     choice = min(results, key=results.get)
-    cx.cx_set_tile_rows(sim.h, choice)
-    _store(key, {"choice": choice, "us_per_step": results[choice] * 1e6})
+    cx.cx_set_time_block(sim.h, choice[0])
+    cx.cx_set_tile_rows(sim.h, choice[1])
+    _store(key, {"choice": list(choice), "us_per_step": results[choice] * 1e6})
     return choice, results

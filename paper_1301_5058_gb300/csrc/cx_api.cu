@@ -144,16 +144,11 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     const long long align = 128 / (long long)c->elem;  // rows start on 128-byte lines
     c->pitch = ((long long)g->nx + align - 1) / align * align;
     c->dt = dt;
-    // default tile height: 32 rows, or fewer so that a small grid still
-    // launches about four 512-column tiles per SM (152 SMs) instead of a
-    // handful of long, latency-bound marches
-    {
-        const long long tiles_x = ((long long)g->nx + 511) / 512;
-        long long rows = ((long long)g->ny * tiles_x + 4 * 152 - 1) / (4 * 152);
-        rows = rows < 1 ? 1 : (rows > 32 ? 32 : rows);
-        while (((long long)g->ny + rows - 1) / rows > 65535) ++rows;
-        c->tile_rows = (int)rows;
-    }
+    c->tile_rows = 0;  // automatic (auto_tile_rows)
+    // two stages per pass pay off for an FP32 state, whose pass is bound by
+    // memory and instruction issue; the FP64 pass is bound by the FP64 pipe
+    // and the fused pass's overlap lanes only add FP64 work
+    c->time_block = c->prec == CX_PREC_F32 ? 2 : 1;
     c->stream = nullptr;
     cudaGetDevice(&c->device);
     const size_t bytes = (size_t)c->pitch * (size_t)g->ny * c->elem;
@@ -285,6 +280,23 @@ int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit)
     return CX_OK;
 }
 
+// Automatic tile height: 32 rows per tile for one stage per pass, 64 for two
+// (the fused march's first and last tile rows repeat work of the neighbour
+// tiles), or fewer so that a small grid still launches about four tiles per
+// SM (152 SMs) instead of a handful of long, latency-bound marches.
+static int auto_tile_rows(const cx_ctx *c)
+{
+    const long long cols = c->time_block == 2 ? 480 : 512;
+    const long long cap = c->time_block == 2 ? 64 : 32;
+    const long long tiles_x = ((long long)c->g.nx + cols - 1) / cols;
+    long long rows = ((long long)c->g.ny * tiles_x + 4 * 152 - 1) / (4 * 152);
+    rows = rows < 1 ? 1 : (rows > cap ? cap : rows);
+    while (((long long)c->g.ny + rows - 1) / rows > 65535) ++rows;
+    return (int)rows;
+}
+
+static int tile_rows_of(const cx_ctx *c) { return c->tile_rows > 0 ? c->tile_rows : auto_tile_rows(c); }
+
 int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
 {
     if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
@@ -330,7 +342,7 @@ int cx_step(cx_ctx *c, int64_t n_steps)
     a.pitch = c->pitch;
     a.law = c->p.chemo_law;
     a.mob = c->p.mobility;
-    a.rows = c->tile_rows;
+    a.rows = tile_rows_of(c);
     a.k = coef_of(c);
     a.sg.per_step = c->p.noise_mode == CX_NOISE_PER_STEP;
     a.sg.dist = c->p.noise_dist;
@@ -339,7 +351,25 @@ int cx_step(cx_ctx *c, int64_t n_steps)
     a.sg.seed = c->seed;
     a.s = c->sigma;
     const bool heun = c->p.scheme == CX_SCHEME_HEUN;
-    for (int64_t m = 0; m < n_steps; ++m) {
+    int64_t m = 0;
+    if (c->time_block == 2) {
+        // two stages per pass: two Euler steps, or one whole Heun step
+        const int64_t per_pass = heun ? 1 : 2;
+        for (; m + per_pass <= n_steps; m += per_pass) {
+            a.b = c->b[c->cur];
+            a.n = c->n[c->cur];
+            a.bu = a.nu = nullptr;
+            a.bo = c->b[c->cur ^ 1];
+            a.no = c->n[c->cur ^ 1];
+            a.stage = 0;
+            a.step = c->step;
+            cudaError_t e = cx::launch_fused(c->prec, a, heun ? 1 : 0, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "fused step kernel launch");
+            c->cur ^= 1;
+            c->step += per_pass;
+        }
+    }
+    for (; m < n_steps; ++m) {
         // Euler step, or Heun's first stage u* = u + dt r(u), into the other buffer
         a.b = c->b[c->cur];
         a.n = c->n[c->cur];
@@ -551,6 +581,10 @@ int cx_set_tile_rows(cx_ctx *c, int32_t rows)
 {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (rows == 0) {  // back to the automatic height
+        c->tile_rows = 0;
+        return CX_OK;
+    }
     if (rows < 1 || rows > 4096 || ((long long)c->g.ny + rows - 1) / rows > 65535)
         return fail(CX_ERR_INVALID_ARG, "tile rows %d outside 1..4096 or too small for ny = %d",
                     rows, c->g.ny);
@@ -563,7 +597,26 @@ int cx_get_tile_rows(cx_ctx *c, int32_t *rows)
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!rows) return fail(CX_ERR_INVALID_ARG, "rows must not be NULL");
-    *rows = c->tile_rows;
+    *rows = tile_rows_of(c);
+    return CX_OK;
+}
+
+int cx_set_time_block(cx_ctx *c, int32_t stages)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (stages != 1 && stages != 2)
+        return fail(CX_ERR_INVALID_ARG, "time block %d: must be 1 or 2 stages per pass", stages);
+    c->time_block = stages;
+    return CX_OK;
+}
+
+int cx_get_time_block(cx_ctx *c, int32_t *stages)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!stages) return fail(CX_ERR_INVALID_ARG, "stages must not be NULL");
+    *stages = c->time_block;
     return CX_OK;
 }
 

@@ -71,6 +71,10 @@ cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long p
 cudaError_t launch_initial_state(int prec, void *b, void *n, int nx, int ny, long long pitch,
                                  double dx, double n0, double bM, double r0sq, cudaStream_t st);
 cudaError_t launch_step(int prec, const StepArgs &a, cudaStream_t st);
+// Two stages in one pass (cx_fused.cu): heun 0 takes the Euler steps a.step
+// and a.step + 1, heun 1 the Heun step a.step; reads (b, n, s), writes
+// (bo, no), which must be other buffers.  bu / nu / stage are not used.
+cudaError_t launch_fused(int prec, const StepArgs &a, int heun, cudaStream_t st);
 
 struct DiagScratch {
     double *partials;  // [blocks][8]
@@ -132,7 +136,8 @@ struct cx_ctx {
     double dt;
     cudaStream_t stream;
     int device;
-    int tile_rows;        // rows per step-kernel tile
+    int tile_rows;        // rows per step-kernel tile (0: automatic)
+    int time_block;       // explicit stages per pass over the grid (1 or 2)
     cx::DiagScratch diag;
     double *h_diag;       // pinned [8]
 };

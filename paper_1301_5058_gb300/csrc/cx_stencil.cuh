@@ -71,6 +71,12 @@ template <> struct Vec<double> {
 __device__ __forceinline__ float div_w(float c, float q) { return __fdividef(c, q); }
 __device__ __forceinline__ double div_w(double c, double q) { return c / q; }
 
+// The last product of a face flux is rounded on its own (never contracted
+// into the additions of the divergence), so a face value does not depend on
+// the code around it and every kernel that evaluates a face gets the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T> struct CoefT {
     T cA, cChi, cG, cR, cN;
 };
@@ -130,12 +136,12 @@ __device__ __forceinline__ void face(T sL, T sR, T nL, T nR, T bL, T bR, const C
     }
     const T a = k.cA * s2 * n2;
     if (MOB == CX_MOBILITY_CENTRAL) {
-        phi = a * b2 * (db - hc * b2 * dn);
+        phi = mul_rn(a * b2, db - hc * b2 * dn);
     } else {
         const T bd = (dn >= T(0)) ? bL : bR;  // donor: the lower-n side
-        phi = a * (b2 * db - T(4) * hc * bd * bd * dn);
+        phi = mul_rn(a, b2 * db - T(4) * hc * bd * bd * dn);
     }
-    g = k.cG * dn;
+    g = mul_rn(k.cG, dn);
 }
 
 template <typename T> struct Row {

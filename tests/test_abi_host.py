@@ -123,7 +123,8 @@ def test_create_rejects_unstable_dt(cx):
 
 def test_null_handles_are_rejected(cx):
     for f, args in ((cx.lib().cx_step, (None, 1)), (cx.lib().cx_synchronize, (None,)),
-                    (cx.lib().cx_set_tile_rows, (None, 2)), (cx.lib().cx_set_step, (None, 0))):
+                    (cx.lib().cx_set_tile_rows, (None, 2)), (cx.lib().cx_set_step, (None, 0)),
+                    (cx.lib().cx_set_time_block, (None, 2)), (cx.lib().cx_get_time_block, (None, None))):
         assert f(*args) == cx.CX_ERR_INVALID_ARG
     cx.lib().cx_destroy(None)  # no-op
 
