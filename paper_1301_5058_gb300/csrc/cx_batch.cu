@@ -52,7 +52,7 @@ __device__ __forceinline__ void tile_step(const InstDev<T> *__restrict__ inst, c
     const InstDev<T> &I = inst[w.x];
     const int nx = I.nx, ny = I.ny;
     const long long pitch = I.pitch;
-    const CoefT<T> k = I.k;
+    const KV<P2<T>> k = make_kv(I.k);
     Ptrs<T> P;
     if (STAGE == 0) {
         P = Ptrs<T>{I.b[parity], I.n[parity], I.s, nullptr, nullptr, I.b[parity ^ 1],
@@ -125,8 +125,13 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long spin_lim
 // Several steps of a group of instances in one cooperative launch: the
 // group's tiles are dealt to the resident blocks, and a grid barrier
 // separates the steps (and Heun's stages).  Loads go through L2 only.
+// Register budget: 2 blocks per SM (the launch sizes its grid from the
+// occupancy this leaves).  The kernel inlines every march variant; its FP64
+// Heun forms still spill a little at 255 registers.
+template <typename T> constexpr int resident_min_blocks() { return 2; }
+
 template <typename T, int LAW, int MOB, int HEUN>
-__global__ void __launch_bounds__(kThreads, 4)  // up to 128 registers: no spills
+__global__ void __launch_bounds__(kThreads, resident_min_blocks<T>())
     batch_resident_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                           int nwork, int parity, int rows, int nsteps, GridBarrier *gb,
                           long long spin_limit)
@@ -147,8 +152,15 @@ __global__ void __launch_bounds__(kThreads, 4)  // up to 128 registers: no spill
 
 // stage 0: u_out(parity^1) = u(parity) + dt r(u(parity))
 // stage 1: u(parity) = (u(parity) + u*(parity^1) + dt r(u*)) / 2, in place
+// As the single-grid step kernel: FP32 Euler steps are bound by HBM
+// bandwidth (64 registers, 8 blocks per SM); Heun's second stage 4; FP64 2.
+template <typename T, int STAGE> constexpr int batch_min_blocks()
+{
+    return sizeof(T) == 4 ? (STAGE == 0 ? 8 : 4) : 2;
+}
+
 template <typename T, int LAW, int MOB, int STAGE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
     batch_step_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                       int parity, int rows)
 {

@@ -66,20 +66,239 @@ template <> struct Vec<double> {
     }
 };
 
-// c / q for the receptor-law weight; FP32 uses the fast reciprocal (the FP32
-// path is judged by tolerance), FP64 the IEEE division.
-__device__ __forceinline__ float div_w(float c, float q) { return __fdividef(c, q); }
-__device__ __forceinline__ double div_w(double c, double q) { return c / q; }
+// ---------------------------------------------------------------------------
+// Arithmetic with every rounding explicit, on one cell (float, double) or on
+// a pair of cells (float2, double2).  The FP32 pair forms are Blackwell's
+// paired FP32 instructions (one issue slot for two cells); each component
+// rounds exactly as the scalar form, so a pair and two scalars give the same
+// bits.  No operation is contracted by the compiler, so a face value or an
+// update is the same bits in every kernel that evaluates it.
 
-// The last product of a face flux is rounded on its own (never contracted
-// into the additions of the divergence), so a face value does not depend on
-// the code around it and every kernel that evaluates a face gets the same bits.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+template <typename T> using P2 = typename PairOf<T>::type;
+
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float2 add_rn(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add_rn(double2 a, double2 b)
+{
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float2 mul_rn(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 mul_rn(double2 a, double2 b)
+{
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 fma_rn(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma_rn(double2 a, double2 b, double2 c)
+{
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+// a - b; the pair form is fma(b, -1, a), which rounds the exact difference
+// once, as the scalar subtraction does (m1 holds -1)
+__device__ __forceinline__ float sub_rn(float a, float b, float) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b, double) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float2 sub_rn(float2 a, float2 b, float2 m1) { return __ffma2_rn(b, m1, a); }
+__device__ __forceinline__ double2 sub_rn(double2 a, double2 b, double2)
+{
+    return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
+// c / q for the receptor-law weight: FP32 the fast division (the FP32 path is
+// judged by tolerance), FP64 the IEEE division
+__device__ __forceinline__ float div_w(float c, float q) { return __fdividef(c, q); }
+__device__ __forceinline__ double div_w(double c, double q) { return c / q; }
+__device__ __forceinline__ float2 div_w(float2 c, float2 q)
+{
+    return make_float2(__fdividef(c.x, q.x), __fdividef(c.y, q.y));
+}
+__device__ __forceinline__ double2 div_w(double2 c, double2 q)
+{
+    return make_double2(c.x / q.x, c.y / q.y);
+}
+// donor-cell b: the side with the lower n (dn = nR - nL)
+__device__ __forceinline__ float donor(float dn, float bL, float bR) { return dn >= 0.f ? bL : bR; }
+__device__ __forceinline__ double donor(double dn, double bL, double bR) { return dn >= 0.0 ? bL : bR; }
+__device__ __forceinline__ float2 donor(float2 dn, float2 bL, float2 bR)
+{
+    return make_float2(donor(dn.x, bL.x, bR.x), donor(dn.y, bL.y, bR.y));
+}
+__device__ __forceinline__ double2 donor(double2 dn, double2 bL, double2 bR)
+{
+    return make_double2(donor(dn.x, bL.x, bR.x), donor(dn.y, bL.y, bR.y));
+}
+__host__ __device__ __forceinline__ float2 pair(float x, float y) { return make_float2(x, y); }
+__host__ __device__ __forceinline__ double2 pair(double x, double y) { return make_double2(x, y); }
 
+// The scaled flux coefficients (dt folded in) as stored per grid.
 template <typename T> struct CoefT {
     T cA, cChi, cG, cR, cN;
 };
+
+// The coefficients and constants of the face and update arithmetic, for
+// one cell (V = T) or a pair (V = P2<T>): signs are folded in so that every
+// subtraction of a product is one multiply-add.
+template <typename V> struct KV {
+    V cA;     // mobility factor
+    V ncChi;  // -chi0 scale
+    V cG;     // nutrient diffusion
+    V cR;     // growth
+    V ncN;    // -consumption
+    V two, four, m1, half;
+};
+template <typename T> __host__ __device__ __forceinline__ KV<P2<T>> make_kv(const CoefT<T> &k)
+{
+    KV<P2<T>> v;
+    v.cA = pair(k.cA, k.cA);
+    v.ncChi = pair(-k.cChi, -k.cChi);
+    v.cG = pair(k.cG, k.cG);
+    v.cR = pair(k.cR, k.cR);
+    v.ncN = pair(-k.cN, -k.cN);
+    v.two = pair(T(2), T(2));
+    v.four = pair(T(4), T(4));
+    v.m1 = pair(T(-1), T(-1));
+    v.half = pair(T(0.5), T(0.5));
+    return v;
+}
+template <typename T> __device__ __forceinline__ KV<T> scalar_kv(const KV<P2<T>> &k)
+{
+    return KV<T>{k.cA.x, k.ncChi.x, k.cG.x, k.cR.x, k.ncN.x, k.two.x, k.four.x, k.m1.x, k.half.x};
+}
+
+// Scaled fluxes (phi, g) through the face between L (left/lower) and R,
+// for one face or a pair of faces:
+//   phi = cA s2 n2 b2 (db - hc b2 dn)          (central b^2 mobility)
+//   phi = cA s2 n2 (b2 db - 4 hc bd^2 dn)       (donor-cell b^2)
+//   g   = cG dn
+// with s2 = sL + sR (likewise n2, b2), db = bR - bL, dn = nR - nL and
+// hc = cChi / (2 + n2)^2 (receptor law) or cChi (constant chi).
+template <int LAW, int MOB, typename V>
+__device__ __forceinline__ void face(V sL, V sR, V nL, V nR, V bL, V bR, const KV<V> &k, V &phi,
+                                     V &g)
+{
+    const V s2 = add_rn(sL, sR), n2 = add_rn(nL, nR), b2 = add_rn(bL, bR);
+    const V db = sub_rn(bR, bL, k.m1), dn = sub_rn(nR, nL, k.m1);
+    V hcn = k.ncChi;  // -hc
+    if (LAW == CX_CHEMO_RECEPTOR) {
+        const V q = add_rn(n2, k.two);
+        hcn = div_w(k.ncChi, mul_rn(q, q));
+    }
+    const V a = mul_rn(mul_rn(k.cA, s2), n2);
+    if (MOB == CX_MOBILITY_CENTRAL) {
+        phi = mul_rn(mul_rn(a, b2), fma_rn(mul_rn(hcn, b2), dn, db));
+    } else {
+        const V bd = donor(dn, bL, bR);
+        phi = mul_rn(a, fma_rn(mul_rn(mul_rn(mul_rn(k.four, hcn), bd), bd), dn, mul_rn(b2, db)));
+    }
+    g = mul_rn(k.cG, dn);
+}
+
+// Four adjacent cells x0..x0+3 of one field, held as the pairs
+// E = (x0, x0+2) and O = (x0+1, x0+3), so that the x-faces pair up too.
+template <typename T> struct Cells {
+    P2<T> E, O;
+};
+template <typename T> __device__ __forceinline__ Cells<T> split4(const T (&v)[4])
+{
+    return Cells<T>{pair(v[0], v[2]), pair(v[1], v[3])};
+}
+template <typename T> __device__ __forceinline__ void join4(const Cells<T> &c, T (&v)[4])
+{
+    v[0] = c.E.x; v[1] = c.O.x; v[2] = c.E.y; v[3] = c.O.y;
+}
+template <typename T> __device__ __forceinline__ Cells<T> zero_cells()
+{
+    return Cells<T>{pair(T(0), T(0)), pair(T(0), T(0))};
+}
+
+// y-faces of four cells (between a row and the next one), as E / O pairs.
+template <typename T> struct YFaces {
+    P2<T> phE, phO, gE, gO;
+};
+template <typename T> __device__ __forceinline__ YFaces<T> zero_yfaces()
+{
+    const P2<T> z = pair(T(0), T(0));
+    return YFaces<T>{z, z, z, z};
+}
+template <typename T, int LAW, int MOB>
+__device__ __forceinline__ YFaces<T> row_yfaces(const Cells<T> &sL, const Cells<T> &nL,
+                                                const Cells<T> &bL, const Cells<T> &sU,
+                                                const Cells<T> &nU, const Cells<T> &bU,
+                                                const KV<P2<T>> &k)
+{
+    YFaces<T> y;
+    face<LAW, MOB>(sL.E, sU.E, nL.E, nU.E, bL.E, bU.E, k, y.phE, y.gE);
+    face<LAW, MOB>(sL.O, sU.O, nL.O, nU.O, bL.O, bU.O, k, y.phO, y.gO);
+    return y;
+}
+
+// x-faces of four cells: f_c lies between cells x0+c-1 and x0+c.  They are
+// computed as A = (f0, f2), B = (f1, f3) and f4; (l*, r*) are the cells
+// x0-1 and x0+4.  Faces on the walls (and past the row's end) carry zero
+// flux unless INTERIOR (no wall within reach).
+template <typename T> struct XFaces {
+    P2<T> phA, gA, phB, gB;
+    T ph4, g4;
+};
+template <typename T, int LAW, int MOB, bool INTERIOR>
+__device__ __forceinline__ XFaces<T> row_xfaces(const Cells<T> &s, const Cells<T> &n,
+                                                const Cells<T> &b, T ls, T ln, T lb, T rs, T rn,
+                                                T rb, const KV<P2<T>> &k, int x0, int nx)
+{
+    XFaces<T> f;
+    face<LAW, MOB>(pair(ls, s.O.x), s.E, pair(ln, n.O.x), n.E, pair(lb, b.O.x), b.E, k, f.phA, f.gA);
+    face<LAW, MOB>(s.E, s.O, n.E, n.O, b.E, b.O, k, f.phB, f.gB);
+    face<LAW, MOB>(s.O.y, rs, n.O.y, rn, b.O.y, rb, scalar_kv<T>(k), f.ph4, f.g4);
+    if (!INTERIOR) {
+        if (x0 == 0) f.phA.x = f.gA.x = T(0);           // west wall
+        if (x0 + 1 >= nx) f.phB.x = f.gB.x = T(0);      // east wall and padding
+        if (x0 + 2 >= nx) f.phA.y = f.gA.y = T(0);
+        if (x0 + 3 >= nx) f.phB.y = f.gB.y = T(0);
+        if (x0 + 4 >= nx) f.ph4 = f.g4 = T(0);
+    }
+    return f;
+}
+
+// u + div + reaction for one pair of cells: faces west/east and, in march
+// order, behind/ahead (DIR +1: ahead is north).
+template <typename T, int DIR>
+__device__ __forceinline__ void cell_update(P2<T> b, P2<T> n, P2<T> phW, P2<T> gW, P2<T> phE,
+                                            P2<T> gE, P2<T> phB, P2<T> gB, P2<T> phA, P2<T> gA,
+                                            const KV<P2<T>> &k, P2<T> &ob, P2<T> &on)
+{
+    const P2<T> phN = DIR > 0 ? phA : phB, phS = DIR > 0 ? phB : phA;
+    const P2<T> gN = DIR > 0 ? gA : gB, gS = DIR > 0 ? gB : gA;
+    const P2<T> r = mul_rn(n, b);
+    const P2<T> divb = add_rn(sub_rn(phE, phW, k.m1), sub_rn(phN, phS, k.m1));
+    const P2<T> divn = add_rn(sub_rn(gE, gW, k.m1), sub_rn(gN, gS, k.m1));
+    ob = fma_rn(k.cR, r, add_rn(b, divb));
+    on = fma_rn(k.ncN, r, add_rn(n, divn));
+}
+// the four cells: even cells lie between A (west) and B (east), odd cells
+// between B and (f2, f4)
+template <typename T, int DIR>
+__device__ __forceinline__ void row_update(const Cells<T> &b, const Cells<T> &n,
+                                           const XFaces<T> &x, const YFaces<T> &yB,
+                                           const YFaces<T> &yA, const KV<P2<T>> &k, Cells<T> &ob,
+                                           Cells<T> &on)
+{
+    cell_update<T, DIR>(b.E, n.E, x.phA, x.gA, x.phB, x.gB, yB.phE, yB.gE, yA.phE, yA.gE, k, ob.E,
+                        on.E);
+    cell_update<T, DIR>(b.O, n.O, x.phB, x.gB, pair(x.phA.y, x.ph4), pair(x.gA.y, x.g4), yB.phO,
+                        yB.gO, yA.phO, yA.gO, k, ob.O, on.O);
+}
+// Heun's second stage: (u0 + u) / 2
+template <typename T>
+__device__ __forceinline__ Cells<T> heun_mean(const Cells<T> &u0, const Cells<T> &u,
+                                              const KV<P2<T>> &k)
+{
+    return Cells<T>{mul_rn(k.half, add_rn(u0.E, u.E)), mul_rn(k.half, add_rn(u0.O, u.O))};
+}
 
 // Per-step noise: the sigma recipe of the state's precision.
 template <typename T> struct NoiseT;
@@ -122,34 +341,6 @@ template <> struct NoiseT<double> {
     }
 };
 
-// Scaled fluxes (phi, g) through the face between L (left/lower) and R.
-template <typename T, int LAW, int MOB>
-__device__ __forceinline__ void face(T sL, T sR, T nL, T nR, T bL, T bR, const CoefT<T> &k,
-                                     T &phi, T &g)
-{
-    const T s2 = sL + sR, n2 = nL + nR, b2 = bL + bR;
-    const T db = bR - bL, dn = nR - nL;
-    T hc = k.cChi;  // chi(n_f) / 2
-    if (LAW == CX_CHEMO_RECEPTOR) {
-        const T q = T(2) + n2;
-        hc = div_w(k.cChi, q * q);
-    }
-    const T a = k.cA * s2 * n2;
-    if (MOB == CX_MOBILITY_CENTRAL) {
-        phi = mul_rn(a * b2, db - hc * b2 * dn);
-    } else {
-        const T bd = (dn >= T(0)) ? bL : bR;  // donor: the lower-n side
-        phi = mul_rn(a, b2 * db - T(4) * hc * bd * bd * dn);
-    }
-    g = mul_rn(k.cG, dn);
-}
-
-template <typename T> struct Row {
-    T b[kCells], n[kCells], s[kCells];
-    T hb, hn, hs;              // lane 0: cell x0-1; lane 31: cell x0+4
-    T ub[kCells], un[kCells];  // STAGE 1: the state at the start of the step
-};
-
 template <typename T> struct Ptrs {
     const T *__restrict__ b;
     const T *__restrict__ n;
@@ -160,20 +351,26 @@ template <typename T> struct Ptrs {
     T *no;
 };
 
+template <typename T> struct Row {
+    Cells<T> b, n, s;
+    T hb, hn, hs;     // lane 0: cell x0-1; lane 31: cell x0+4
+    Cells<T> ub, un;  // STAGE 1: the state at the start of the step
+};
+
 // One thread's march over rows j0..jend-1 in direction DIR (+1: increasing j,
-// -1: decreasing j).  The y-face shared with the row processed before
-// ("behind") is carried in registers; the y-face with the next row in march
-// order ("ahead") is computed from the row loaded in this iteration.  Face
-// values do not depend on DIR (a face is always evaluated with L the lower
-// row), so both directions give bit-identical results.  CG: read through L2
-// only (a persistent launch whose blocks read what other blocks wrote
-// earlier in the same launch).  INTERIOR: the caller guarantees that every
-// thread's cells and both x-neighbours of the warp lie inside the grid
+// -1: decreasing j).  The y-faces shared with the row processed before
+// ("behind") are carried in registers; the y-faces with the next row in
+// march order ("ahead") are computed from the row loaded in this iteration.
+// Face values do not depend on DIR (a face is always evaluated with L the
+// lower row), so both directions give bit-identical results.  CG: read
+// through L2 only (a persistent launch whose blocks read what other blocks
+// wrote earlier in the same launch).  INTERIOR: the caller guarantees that
+// every thread's cells and both x-neighbours of the warp lie inside the grid
 // (0 < x0 and x0 + 4 < nx for all threads), so the x-wall tests drop out.
 template <typename T, int LAW, int MOB, int NOISE, int STAGE, int DIR, bool CG = false,
           bool INTERIOR = false>
 __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long long pitch,
-                                      const CoefT<T> &k, const NoiseT<T> &nz, int x0, int j0,
+                                      const KV<P2<T>> &k, const NoiseT<T> &nz, int x0, int j0,
                                       int jend)
 {
     const int lane = threadIdx.x & 31;
@@ -185,24 +382,28 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
     const bool halo = halo_l || halo_r;
     const long long xh = halo_l ? (long long)x0 - 1 : (long long)x0 + kCells;
 
-    auto vload = [](const T *p, T (&v)[kCells]) {
+    auto vload = [](const T *p) -> Cells<T> {
+        T v[kCells];
         if (CG) Vec<T>::load_cg(p, v);
         else Vec<T>::load(p, v);
+        return split4(v);
     };
     auto sload = [](const T *p) -> T { return CG ? __ldcg(p) : __ldg(p); };
     auto load_row = [&](int r, Row<T> &R, bool own) {
         const long long off = (long long)r * pitch;
-        vload(P.b + off + xv, R.b);
-        vload(P.n + off + xv, R.n);
+        R.b = vload(P.b + off + xv);
+        R.n = vload(P.n + off + xv);
         if (NOISE == 0) {
-            vload(P.s + off + xv, R.s);
+            R.s = vload(P.s + off + xv);
         } else {
-            nz.four((long long)r * nx + x0, R.s);
+            T v[kCells];
+            nz.four((long long)r * nx + x0, v);
             if (!INTERIOR) {
 #pragma unroll
                 for (int c = 0; c < kCells; ++c)
-                    if (x0 + c >= nx) R.s[c] = T(0);  // past the row's end
+                    if (x0 + c >= nx) v[c] = T(0);  // past the row's end
             }
+            R.s = split4(v);
         }
         R.hb = R.hn = R.hs = T(0);
         if (halo) {
@@ -211,35 +412,31 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
             R.hs = NOISE == 0 ? sload(P.s + off + xh) : nz.at((long long)r * nx + xh);
         }
         if (STAGE == 1 && own) {
-            if (CG) {
-                Vec<T>::load_cg(P.bu + off + xv, R.ub);
-                Vec<T>::load_cg(P.nu + off + xv, R.un);
-            } else {
-                Vec<T>::load_rw(P.bu + off + xv, R.ub);
-                Vec<T>::load_rw(P.nu + off + xv, R.un);
-            }
+            T v[kCells];
+            if (CG) Vec<T>::load_cg(P.bu + off + xv, v);
+            else Vec<T>::load_rw(P.bu + off + xv, v);
+            R.ub = split4(v);
+            if (CG) Vec<T>::load_cg(P.nu + off + xv, v);
+            else Vec<T>::load_rw(P.nu + off + xv, v);
+            R.un = split4(v);
         }
     };
-    // y-face between a lower row lo and an upper row hi
-    auto yface = [&](const Row<T> &lo, const Row<T> &hi, T (&ph)[kCells], T (&g)[kCells]) {
-#pragma unroll
-        for (int c = 0; c < kCells; ++c)
-            face<T, LAW, MOB>(lo.s[c], hi.s[c], lo.n[c], hi.n[c], lo.b[c], hi.b[c], k, ph[c], g[c]);
+    // y-faces between a lower row lo and an upper row hi
+    auto yfaces = [&](const Row<T> &lo, const Row<T> &hi) {
+        return row_yfaces<T, LAW, MOB>(lo.s, lo.n, lo.b, hi.s, hi.n, hi.b, k);
     };
 
     const int jfirst = DIR > 0 ? j0 : jend - 1;
     const int jbehind = jfirst - DIR;
     Row<T> cur, nxt;
-    T phB[kCells], gB[kCells];
+    YFaces<T> yB;
     load_row(jfirst, cur, true);
     if (jbehind >= 0 && jbehind < ny) {
         Row<T> prv;
         load_row(jbehind, prv, false);
-        if (DIR > 0) yface(prv, cur, phB, gB);
-        else yface(cur, prv, phB, gB);
+        yB = DIR > 0 ? yfaces(prv, cur) : yfaces(cur, prv);
     } else {
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) phB[c] = gB[c] = T(0);  // wall behind
+        yB = zero_yfaces<T>();  // wall behind
     }
 
     const int rows = jend - j0;
@@ -250,72 +447,46 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
         if (has_a) load_row(ja, nxt, it + 1 < rows);
 
         // x-neighbours of this thread's 4 cells
-        T lb = __shfl_up_sync(kFull, cur.b[kCells - 1], 1);
-        T ln = __shfl_up_sync(kFull, cur.n[kCells - 1], 1);
-        T ls = __shfl_up_sync(kFull, cur.s[kCells - 1], 1);
-        T rb = __shfl_down_sync(kFull, cur.b[0], 1);
-        T rn = __shfl_down_sync(kFull, cur.n[0], 1);
-        T rs = __shfl_down_sync(kFull, cur.s[0], 1);
+        T lb = __shfl_up_sync(kFull, cur.b.O.y, 1);
+        T ln = __shfl_up_sync(kFull, cur.n.O.y, 1);
+        T ls = __shfl_up_sync(kFull, cur.s.O.y, 1);
+        T rb = __shfl_down_sync(kFull, cur.b.E.x, 1);
+        T rn = __shfl_down_sync(kFull, cur.n.E.x, 1);
+        T rs = __shfl_down_sync(kFull, cur.s.E.x, 1);
         if (lane == 0) { lb = cur.hb; ln = cur.hn; ls = cur.hs; }
         if (lane == 31) { rb = cur.hb; rn = cur.hn; rs = cur.hs; }
+        const XFaces<T> xf =
+            row_xfaces<T, LAW, MOB, INTERIOR>(cur.s, cur.n, cur.b, ls, ln, lb, rs, rn, rb, k, x0, nx);
 
-        // x-faces: f[c] lies between cells x0+c-1 and x0+c
-        T phX[kCells + 1], gX[kCells + 1];
-        face<T, LAW, MOB>(ls, cur.s[0], ln, cur.n[0], lb, cur.b[0], k, phX[0], gX[0]);
-#pragma unroll
-        for (int c = 1; c < kCells; ++c)
-            face<T, LAW, MOB>(cur.s[c - 1], cur.s[c], cur.n[c - 1], cur.n[c], cur.b[c - 1],
-                              cur.b[c], k, phX[c], gX[c]);
-        face<T, LAW, MOB>(cur.s[kCells - 1], rs, cur.n[kCells - 1], rn, cur.b[kCells - 1], rb, k,
-                          phX[kCells], gX[kCells]);
-        if (!INTERIOR) {
-            if (x0 == 0) phX[0] = gX[0] = T(0);  // west wall
-#pragma unroll
-            for (int c = 1; c <= kCells; ++c)
-                if (x0 + c >= nx) phX[c] = gX[c] = T(0);  // east wall (and padding)
-        }
+        // y-faces with the row ahead (a wall past the grid's first/last row)
+        YFaces<T> yA;
+        if (has_a) yA = DIR > 0 ? yfaces(cur, nxt) : yfaces(nxt, cur);
+        else yA = zero_yfaces<T>();
 
-        // y-face with the row ahead (a wall past the grid's first/last row)
-        T phA[kCells], gA[kCells];
-        if (has_a) {
-            if (DIR > 0) yface(cur, nxt, phA, gA);
-            else yface(nxt, cur, phA, gA);
-        } else {
-#pragma unroll
-            for (int c = 0; c < kCells; ++c) phA[c] = gA[c] = T(0);
+        Cells<T> ob, on;
+        row_update<T, DIR>(cur.b, cur.n, xf, yB, yA, k, ob, on);
+        if (STAGE == 1) {
+            ob = heun_mean(cur.ub, ob, k);
+            on = heun_mean(cur.un, on, k);
         }
-
-        T ob[kCells], on[kCells];
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) {
-            const T phN = DIR > 0 ? phA[c] : phB[c], phS = DIR > 0 ? phB[c] : phA[c];
-            const T gN = DIR > 0 ? gA[c] : gB[c], gS = DIR > 0 ? gB[c] : gA[c];
-            const T r = cur.n[c] * cur.b[c];
-            const T divb = (phX[c + 1] - phX[c]) + (phN - phS);
-            const T divn = (gX[c + 1] - gX[c]) + (gN - gS);
-            ob[c] = (cur.b[c] + divb) + k.cR * r;
-            on[c] = (cur.n[c] + divn) - k.cN * r;
-            if (STAGE == 1) {
-                ob[c] = T(0.5) * (cur.ub[c] + ob[c]);
-                on[c] = T(0.5) * (cur.un[c] + on[c]);
-            }
-        }
+        T vb[kCells], vn[kCells];
+        join4(ob, vb);
+        join4(on, vn);
         const long long off = (long long)j * pitch;
         if (INTERIOR || x0 + kCells <= nx) {
-            Vec<T>::store(P.bo + off + x0, ob);
-            Vec<T>::store(P.no + off + x0, on);
+            Vec<T>::store(P.bo + off + x0, vb);
+            Vec<T>::store(P.no + off + x0, vn);
         } else {
 #pragma unroll
             for (int c = 0; c < kCells; ++c)
                 if (x0 + c < nx) {
-                    P.bo[off + x0 + c] = ob[c];
-                    P.no[off + x0 + c] = on[c];
+                    P.bo[off + x0 + c] = vb[c];
+                    P.no[off + x0 + c] = vn[c];
                 }
         }
 
         cur = nxt;
-#pragma unroll
-        for (int c = 0; c < kCells; ++c) { phB[c] = phA[c]; gB[c] = gA[c]; }
+        yB = yA;
     }
 }
 

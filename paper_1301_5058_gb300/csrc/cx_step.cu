@@ -32,9 +32,18 @@ using namespace stencil;
 // neighbouring bands is read by both near the start (or both near the end)
 // of their marches, while it is still in L2, instead of once at the start
 // of one band and again at the end of the other.
+// Resident blocks per SM the register budget is sized for.  FP32 Euler with
+// a static sigma field is bound by HBM bandwidth and needs every warp it can
+// get: 64 registers, 8 blocks (32 warps).  Other FP32 forms: 4 (128
+// registers); FP64 (bound by the FP64 pipe): 2.
+template <typename T, int NOISE, int STAGE> constexpr int step_min_blocks()
+{
+    return sizeof(T) == 4 ? ((NOISE == 0 && STAGE == 0) ? 8 : 4) : 2;
+}
+
 template <typename T, int LAW, int MOB, int NOISE, int STAGE>
-__global__ void __launch_bounds__(kThreads)
-    step_kernel(Ptrs<T> P, int nx, int ny, long long pitch, CoefT<T> k, NoiseT<T> nz, int rows)
+__global__ void __launch_bounds__(kThreads, step_min_blocks<T, NOISE, STAGE>())
+    step_kernel(Ptrs<T> P, int nx, int ny, long long pitch, KV<P2<T>> k, NoiseT<T> nz, int rows)
 {
     const int x0 = (blockIdx.x * kThreads + threadIdx.x) * kCells;
     const int j0 = blockIdx.y * rows;
@@ -57,7 +66,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, int LAW, int MOB, int NOISE, int STAGE>
 cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
 {
-    const CoefT<T> k{(T)a.k.cA, (T)a.k.cChi, (T)a.k.cG, (T)a.k.cR, (T)a.k.cN};
+    const KV<P2<T>> k = make_kv(CoefT<T>{(T)a.k.cA, (T)a.k.cChi, (T)a.k.cG, (T)a.k.cR, (T)a.k.cN});
     NoiseT<T> nz;
     nz.seed = a.sg.seed;
     nz.step = (uint64_t)a.step;
