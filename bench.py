@@ -50,6 +50,23 @@ def launches_per_window(scheme, time_block, S):
     return S if scheme == "euler" else 2 * S
 
 
+# Algorithmic floating-point work per cell-update of the scheme as written
+# (receptor law, central mobility; a multiply-add counts two): 16 flops per
+# face (sums, differences, the receptor weight with one division, the flux
+# products), two faces per cell, 13 for the update; Heun takes two stages and
+# the mean (u0 + u) / 2 of b and n.  Peak rates from the unit counts at the
+# sampled maximum SM clock: 128 FP32 lanes per SM, and for FP64 2
+# multiply-adds per SM and clock (GB300's nominal 1.25 TFLOP/s at 2.07 GHz on
+# 152 SMs), a multiply-add being two flops.
+FLOPS_PER_CELL_UPDATE = {"euler": 2 * 16 + 13, "heun": 2 * (2 * 16 + 13) + 4}
+SMS = 152
+
+
+def alu_peak_tflops(prec, sm_mhz):
+    fma_per_sm = 128 if prec == "f32" else 2
+    return 2 * fma_per_sm * SMS * sm_mhz * 1e6 / 1e12
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,6 +373,37 @@ def main():
     lpw = launches_per_window(args.scheme, args.time_block, S)
     kernel = "fused_kernel" if args.time_block == 2 else "step_kernel"
     achieved = bpc * cells / per_launch / 1e9
+    rate = cells / per_launch  # cell-updates/s of the step kernels alone
+    sm_mhz = r["clocks"].get("sm_max_mhz") or 2070.0
+    alu = {"bound": "alu", "unit": "TFLOP/s",
+           "flops_per_cell_update": FLOPS_PER_CELL_UPDATE[args.scheme],
+           "achieved": FLOPS_PER_CELL_UPDATE[args.scheme] * rate / 1e12,
+           "peak": alu_peak_tflops(args.precision, sm_mhz),
+           "peak_kind": f"derived: {'128 FP32' if args.precision == 'f32' else '2 FP64'} multiply-adds "
+                        f"per SM and clock x {SMS} SMs x {sm_mhz:.0f} MHz"}
+    alu["frac"] = alu["achieved"] / alu["peak"]
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+           "kernel": kernel,
+           "traffic": kernel_traffic(args.precision, kernel),
+           "algorithmic_bytes_per_cell": bpc,
+           "kernel_ms_per_time_step": per_launch * 1e3,
+           # the HBM-roofline rate of a one-step-per-pass stepper
+           # (20 B per FP32 cell-update): temporal blocking may pass it
+           "one_step_pass_roofline_cell_updates_per_s":
+               peak * 1e9 / bytes_per_cell(args.precision, args.scheme, args.noise, 1),
+           "kernel_cell_updates_per_s": rate,
+           "launches_per_time_step": lpw / S}
+    if args.precision == "f64":
+        # the FP64 pass is bound by the FP64 pipe: that is its roofline
+        roofline = dict(alu, kernel=kernel, traffic=hbm["traffic"], kernel_cell_updates_per_s=rate,
+                        kernel_ms_per_time_step=per_launch * 1e3, hbm=hbm)
+    else:
+        roofline = dict(hbm, alu_fp32=alu)
+        if args.time_block == 2:
+            roofline["limiter"] = ("instruction issue: two stages per pass halve the HBM bytes "
+                                   "per cell-update, and the pass then issues about 72 thread "
+                                   "instructions per cell-update (ncu)")
     out = {
         "metric": "grid-cell updates/s",
         "value": value,
@@ -370,18 +418,7 @@ def main():
         "dtype": args.precision,
         "data": "synthetic (seeded sigma field and Gaussian inoculum)",
         "config": config_block(args, cfg),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "kernel": kernel,
-                     "traffic": kernel_traffic(args.precision, kernel),
-                     "algorithmic_bytes_per_cell": bpc,
-                     "kernel_ms_per_time_step": per_launch * 1e3,
-                     # the HBM-roofline rate of a one-step-per-pass stepper
-                     # (20 B per FP32 cell-update): temporal blocking may pass it
-                     "one_step_pass_roofline_cell_updates_per_s":
-                         peak * 1e9 / bytes_per_cell(args.precision, args.scheme, args.noise, 1),
-                     "kernel_cell_updates_per_s": cells / per_launch,
-                     "launches_per_time_step": lpw / S},
+        "roofline": roofline,
         "gpu_launches": K * (lpw + 2),
         "clocks": r["clocks"],
         "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b", "min_n")},
@@ -424,6 +461,7 @@ def main_sweep(args):
     if args.tune:
         autotune.tune_batch(bt, steps=64, reps=2, use_cache=False)
     choice = cx.cx_batch_get_tuning(bt.h)
+    depth = cx.cx_batch_get_time_block(bt.h)
 
     def timed(step_fn, diag_fn, clk=None):
         for _ in range(Wm):
@@ -466,7 +504,8 @@ def main_sweep(args):
     single_total = sum(args.point_steps * single[s["nx"]][0] + single[s["nx"]][1] for s in specs)
     single_pph = args.count * 3600.0 / single_total
     peak, peak_kind = peaks()
-    achieved = 20 * cells / (kernel_s / (K * S)) / 1e9
+    bpc = bytes_per_cell("f32", "euler", "static", depth)
+    achieved = bpc * cells / (kernel_s / (K * S)) / 1e9
     print(json.dumps({
         "metric": "sweep points/hour", "value": batch_pph, "unit": "points/h", "n_gpus": 1,
         "steps": K, "warmup": Wm, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True,
@@ -477,15 +516,17 @@ def main_sweep(args):
                                f"per point", "cells_per_time_step": cells,
                    "time_steps_per_step": S, "tuning": {"tile_rows": choice[0], "graph_steps": choice[1],
                                                         "group_bytes": choice[2],
-                                                        "resident_steps": choice[3]}},
+                                                        "resident_steps": choice[3],
+                                                        "time_block": depth}},
         "cell_updates_per_s": cells / per_step,
         "single_instance_points_per_hour": single_pph,
         "single_instance_ms_per_time_step": {str(k): v[0] * 1e3 for k, v in single.items()},
         "speedup_vs_single_instance": batch_pph / single_pph,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
-                     "algorithmic_bytes_per_cell": 20},
-        "gpu_launches": K * (S + 2),
+                     "kernel": "batch_fused_kernel" if depth == 2 else "batch_step_kernel",
+                     "algorithmic_bytes_per_cell": bpc},
+        "gpu_launches": K * (launches_per_window("euler", depth, S) + 2),
         "clocks": clk.summary(),
     }))
 

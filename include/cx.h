@@ -245,7 +245,8 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
 int cx_batch_set_stream(cx_batch *b, void *stream);
 
 /* Performance knobs, none of which changes any result bit:
- *   tile_rows   rows per tile of the step kernel (1..4096, default 32);
+ *   tile_rows   rows per tile of the step kernel (1..4096, default 32; the
+ *               tiles of both depths);
  *   graph_steps steps captured per CUDA graph and replayed (0: plain
  *               launches; rounded up to even for Euler; default 64);
  *   group_bytes if > 0, instances are cut into consecutive groups whose
@@ -264,6 +265,15 @@ int cx_batch_set_tuning(cx_batch *b, int32_t tile_rows, int32_t graph_steps, int
                         int32_t resident_steps);
 int cx_batch_get_tuning(cx_batch *b, int32_t *tile_rows, int32_t *graph_steps, int64_t *group_bytes,
                         int32_t *resident_steps);
+
+/* Temporal blocking depth of the batch, as cx_set_time_block: 2 takes two
+ * Euler steps (or one whole Heun step) per pass over every instance, on
+ * 480-column tiles; 1 one step per pass.  Results are bit-identical for
+ * both.  Default: 2 for FP32 batches, 1 for FP64.  The resident mode
+ * (resident_steps > 0) takes one stage per pass whatever the depth.
+ * Errors: INVALID_ARG. */
+int cx_batch_set_time_block(cx_batch *b, int32_t stages);
+int cx_batch_get_time_block(cx_batch *b, int32_t *stages);
 
 /* Advance every instance by n_steps >= 0 steps.  Asynchronous. */
 int cx_batch_step(cx_batch *b, int64_t n_steps);

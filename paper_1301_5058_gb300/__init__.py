@@ -95,6 +95,8 @@ _SIGNATURES = {
     "cx_set_tile_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cx_get_tile_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cx_set_time_block": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cx_batch_set_time_block": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cx_batch_get_time_block": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cx_get_time_block": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cx_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(cx_grid),
                                        ctypes.POINTER(cx_params), ctypes.POINTER(ctypes.c_uint64),
@@ -272,6 +274,16 @@ def cx_set_time_block(h, stages: int):
 def cx_get_time_block(h) -> int:
     r = ctypes.c_int32()
     _check(lib().cx_get_time_block(h, ctypes.byref(r)))
+    return r.value
+
+
+def cx_batch_set_time_block(h, stages: int):
+    _check(lib().cx_batch_set_time_block(h, stages))
+
+
+def cx_batch_get_time_block(h) -> int:
+    r = ctypes.c_int32()
+    _check(lib().cx_batch_get_time_block(h, ctypes.byref(r)))
     return r.value
 
 
@@ -531,8 +543,10 @@ class Batch:
     def set_field(self, index, which, arr):
         cx_batch_set_field(self.h, index, which, arr)
 
-    def tune(self, tile_rows, graph_steps, group_bytes, resident_steps=0):
+    def tune(self, tile_rows, graph_steps, group_bytes, resident_steps=0, time_block=None):
         cx_batch_set_tuning(self.h, tile_rows, graph_steps, group_bytes, resident_steps)
+        if time_block is not None:
+            cx_batch_set_time_block(self.h, time_block)
 
     def close(self):
         if getattr(self, "h", None):

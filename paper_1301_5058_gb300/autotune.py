@@ -1,9 +1,10 @@
 """Autotuner for the batched and single-grid steppers.
 
 The knobs change no result bit (include/cx.h): the tile height of the step
-kernel, the number of steps captured per CUDA graph, the size of the
-instance groups a batch runs back to back (to keep a group resident in L2),
-and how many steps a group advances per resident (cooperative) launch.
+kernel, the temporal blocking depth (explicit stages per pass), the number
+of steps captured per CUDA graph, the size of the instance groups a batch
+runs back to back (to keep a group resident in L2), and how many steps a
+group advances per resident (cooperative) launch.
 Each candidate is timed with CUDA events on the handle's stream after a
 warm-up; the fastest is applied and cached in a JSON file keyed by
 precision, scheme and the mix of grid sizes (CX_TUNE_CACHE, default
@@ -19,11 +20,14 @@ import paper_1301_5058_gb300 as cx
 
 L2_BYTES = 126 * 2 ** 20   # GB300 L2 (about 126 MiB usable)
 
-# (tile rows, graph steps, group bytes, resident steps): one launch per step
-# over every instance, or L2-sized groups stepped by resident launches
-BATCH_CANDIDATES = ([(rows, graph, 0, 0) for rows in (8, 16, 32, 64) for graph in (0, 64)] +
-                    [(rows, 0, group, res) for rows in (4, 8, 16)
-                     for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)])
+# (tile rows, graph steps, group bytes, resident steps, stages per pass):
+# one launch per pass over every instance at either depth; L2-sized groups
+# stepped by resident launches (one stage per pass) are searched only when
+# asked for (RESIDENT_CANDIDATES: they have never won on GB300)
+BATCH_CANDIDATES = [(rows, graph, 0, 0, depth) for depth in (1, 2) for rows in (16, 32, 64)
+                    for graph in (0, 64)]
+RESIDENT_CANDIDATES = [(rows, 0, group, res, 1) for rows in (4, 8, 16)
+                       for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)]
 SINGLE_CANDIDATES = (8, 16, 32, 64, 128, 256)
 
 
@@ -73,9 +77,9 @@ def _time_steps(torch, stream, fn, steps: int, reps: int) -> float:
 
 def tune_batch(batch: "cx.Batch", steps: int = 128, reps: int = 3, candidates=None,
                use_cache: bool = True, verbose: bool = False):
-    """Pick (tile_rows, graph_steps, group_bytes) for `batch`, apply it and
-    return (choice, {candidate: seconds per step}).  The timed steps advance
-    the batch's state."""
+    """Pick (tile_rows, graph_steps, group_bytes, resident_steps, stages per
+    pass) for `batch`, apply it and return (choice, {candidate: seconds per
+    step}).  The timed steps advance the batch's state."""
     import torch
     key = batch_key(batch.grids, batch.params)
     if use_cache:
@@ -98,7 +102,7 @@ def tune_batch(batch: "cx.Batch", steps: int = 128, reps: int = 3, candidates=No
         results[cand] = _time_steps(torch, stream, batch.step, steps, reps)
         if verbose:
             print(f"  rows={cand[0]:3d} graph={cand[1]:3d} group={cand[2] >> 20:4d} MiB "
-                  f"resident={cand[3]:4d}: {results[cand] * 1e6:9.1f} us/step")
+                  f"resident={cand[3]:4d} depth={cand[4]}: {results[cand] * 1e6:9.1f} us/step")
     choice = min(results, key=results.get)
     batch.tune(*choice)
     _store(key, {"choice": list(choice), "us_per_step": results[choice] * 1e6})

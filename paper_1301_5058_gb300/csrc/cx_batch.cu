@@ -12,9 +12,12 @@
 // cut into consecutive groups whose fields fit that many bytes (e.g. L2) and
 // each group runs all its steps before the next starts.
 //
+// With two stages per pass (batch_fused_kernel) a second work list holds
+// one entry per 480-column x `rows`-row tile of the two-stage march.
+//
 // Every instance goes through the same per-thread stencil code as a single
-// grid (cx_stencil.cuh), so a batch instance and a cx_ctx with the same
-// grid, parameters and seed give bit-identical fields.
+// grid (cx_stencil.cuh, cx_fused.cuh), so a batch instance and a cx_ctx with
+// the same grid, parameters and seed give bit-identical fields.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -23,6 +26,7 @@
 #include <new>
 #include <vector>
 
+#include "cx_fused.cuh"
 #include "cx_reduce.cuh"
 #include "cx_stencil.cuh"
 
@@ -167,6 +171,49 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
     tile_step<T, LAW, MOB, STAGE, false>(inst, work[blockIdx.x], parity, rows);
 }
 
+// Two stages per pass (two Euler steps, or one Heun step) of one tile of the
+// 480-column work list: reads u(parity), writes u(parity^1).  Register
+// budget as the single-grid two-stage pass (96 registers for FP32 Euler).
+template <typename T, bool HEUN> constexpr int batch_fused_min_blocks()
+{
+    return sizeof(T) == 4 ? (HEUN ? 4 : 5) : 2;
+}
+
+template <typename T, int LAW, int MOB, bool HEUN>
+__global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T, HEUN>())
+    batch_fused_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
+                       int parity, int rows)
+{
+    const int4 w = work[blockIdx.x];
+    const InstDev<T> &I = inst[w.x];
+    const int nx = I.nx, ny = I.ny;
+    const long long pitch = I.pitch;
+    const KV<P2<T>> k = make_kv(I.k);
+    const Ptrs<T> P{I.b[parity], I.n[parity], I.s, nullptr, nullptr, I.b[parity ^ 1],
+                    I.n[parity ^ 1]};
+    const NoiseT<T> nz{};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int xb = w.y * kFusedBlockCols;
+    // warps share nothing: one whose written columns all lie past the row's
+    // end (ragged last tile) leaves at once
+    if (xb + warp * kFusedCols >= nx) return;
+    const int x0 = xb + warp * kFusedCols - kCells + lane * kCells;
+    const int j0 = w.z * rows;
+    const int jend = min(j0 + rows, ny);
+    const bool interior = w.y > 0 && xb + kFusedBlockCols + kCells <= nx;
+    if (w.z & 1) {
+        if (interior)
+            march2<T, LAW, MOB, 0, HEUN, -1, true>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+        else
+            march2<T, LAW, MOB, 0, HEUN, -1, false>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+    } else {
+        if (interior)
+            march2<T, LAW, MOB, 0, HEUN, +1, true>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+        else
+            march2<T, LAW, MOB, 0, HEUN, +1, false>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+    }
+}
+
 // Diagnostics: block (r, i) reduces rows r, r + B, ... of instance i.
 template <typename T>
 __global__ void __launch_bounds__(reduce::kThreads)
@@ -210,6 +257,33 @@ cudaError_t launch_batch_t(const void *inst, const int4 *work, int nwork, int pa
         batch_step_kernel<T, LAW, MOB, 1><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst, work,
                                                                       parity, rows);
     return cudaGetLastError();
+}
+
+template <typename T, int LAW, int MOB>
+cudaError_t launch_fused_t(const void *inst, const int4 *work, int nwork, int parity, int rows,
+                           int heun, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    if (heun)
+        batch_fused_kernel<T, LAW, MOB, true><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst,
+                                                                          work, parity, rows);
+    else
+        batch_fused_kernel<T, LAW, MOB, false><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst,
+                                                                           work, parity, rows);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fused_prec(int law, int mob, const void *inst, const int4 *work, int nwork,
+                              int parity, int rows, int heun, cudaStream_t st)
+{
+    if (law == CX_CHEMO_RECEPTOR)
+        return mob == CX_MOBILITY_CENTRAL
+                   ? launch_fused_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, heun, st)
+                   : launch_fused_t<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, heun, st);
+    return mob == CX_MOBILITY_CENTRAL
+               ? launch_fused_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, heun, st)
+               : launch_fused_t<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, heun, st);
 }
 
 template <typename T>
@@ -291,6 +365,14 @@ cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, cons
     return prec == CX_PREC_F64
                ? launch_batch_prec<double>(law, mob, inst, work, nwork, parity, rows, stage, st)
                : launch_batch_prec<float>(law, mob, inst, work, nwork, parity, rows, stage, st);
+}
+
+cudaError_t launch_batch_fused(int prec, int law, int mob, const void *inst, const int4 *work,
+                               int nwork, int parity, int rows, int heun, cudaStream_t st)
+{
+    return prec == CX_PREC_F64
+               ? launch_fused_prec<double>(law, mob, inst, work, nwork, parity, rows, heun, st)
+               : launch_fused_prec<float>(law, mob, inst, work, nwork, parity, rows, heun, st);
 }
 
 cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,

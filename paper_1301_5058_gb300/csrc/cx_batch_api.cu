@@ -28,6 +28,7 @@ int bcuda(cudaError_t e, const char *what)
     } while (0)
 
 constexpr int kTileCols = 512;       // columns per tile (128 threads x 4 cells)
+constexpr int kFusedTileCols = 480;  // written columns per tile of the two-stage march
 constexpr int kDiagBlocksPerInst = 64;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -47,13 +48,17 @@ struct cx_batch {
     size_t elem = 4;
     void *d_inst = nullptr;
     std::vector<unsigned char> h_inst;
-    int4 *d_work = nullptr;
+    int4 *d_work = nullptr;       // 512-column tiles (one stage per pass)
     std::vector<int> work_begin;  // first work item of each instance (+ total)
+    int4 *d_work2 = nullptr;      // 480-column tiles (two stages per pass)
+    std::vector<int> work2_begin;
     int rows = 32;
     int graph_steps = 64;
     long long group_bytes = 0;
+    int time_block = 1;             // explicit stages per pass (1 or 2)
     std::vector<int> group_first;  // instance index where each group starts (+ count)
-    std::vector<cudaGraphExec_t> gexec;
+    std::vector<cudaGraphExec_t> gexec[2];  // per group, by starting parity
+    std::vector<int> gend[2];               // parity after that graph
     int resident_steps = 0;         // > 0: steps per cooperative launch of a group
     void *d_barrier = nullptr;      // grid barrier state of the resident kernel
     long long spin_limit = 1 << 22; // polls before a barrier wait gives up
@@ -68,9 +73,12 @@ namespace {
 
 void drop_graphs(cx_batch *B)
 {
-    for (auto &e : B->gexec)
-        if (e) cudaGraphExecDestroy(e);
-    B->gexec.clear();
+    for (int p = 0; p < 2; ++p) {
+        for (auto &e : B->gexec[p])
+            if (e) cudaGraphExecDestroy(e);
+        B->gexec[p].clear();
+        B->gend[p].clear();
+    }
 }
 
 void free_batch(cx_batch *B)
@@ -81,6 +89,7 @@ void free_batch(cx_batch *B)
     if (B->arena) cudaFree(B->arena);
     if (B->d_inst) cudaFree(B->d_inst);
     if (B->d_work) cudaFree(B->d_work);
+    if (B->d_work2) cudaFree(B->d_work2);
     if (B->d_part) cudaFree(B->d_part);
     if (B->d_res) cudaFree(B->d_res);
     if (B->h_res) cudaFreeHost(B->h_res);
@@ -89,24 +98,31 @@ void free_batch(cx_batch *B)
     delete B;
 }
 
-// Tile work list for the current tile height, instance by instance.
+// Tile work lists for the current tile height, instance by instance: the
+// one-stage march's 512-column tiles and the two-stage march's 480-column
+// tiles.
 int build_work(cx_batch *B)
 {
-    std::vector<int4> w;
-    B->work_begin.assign(B->count + 1, 0);
-    for (int i = 0; i < B->count; ++i) {
-        B->work_begin[i] = (int)w.size();
-        const int tx = (B->g[i].nx + kTileCols - 1) / kTileCols;
-        const int ty = (B->g[i].ny + B->rows - 1) / B->rows;
-        for (int y = 0; y < ty; ++y)
-            for (int x = 0; x < tx; ++x) w.push_back(make_int4(i, x, y, 0));
+    for (int f = 0; f < 2; ++f) {
+        const int cols = f ? kFusedTileCols : kTileCols;
+        std::vector<int> &begin = f ? B->work2_begin : B->work_begin;
+        int4 *&d = f ? B->d_work2 : B->d_work;
+        std::vector<int4> w;
+        begin.assign(B->count + 1, 0);
+        for (int i = 0; i < B->count; ++i) {
+            begin[i] = (int)w.size();
+            const int tx = (B->g[i].nx + cols - 1) / cols;
+            const int ty = (B->g[i].ny + B->rows - 1) / B->rows;
+            for (int y = 0; y < ty; ++y)
+                for (int x = 0; x < tx; ++x) w.push_back(make_int4(i, x, y, 0));
+        }
+        begin[B->count] = (int)w.size();
+        if (d) cudaFree(d);
+        d = nullptr;
+        BX_CUDA(cudaMalloc((void **)&d, w.size() * sizeof(int4)), "work list allocation");
+        BX_CUDA(cudaMemcpy(d, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice),
+                "work list upload");
     }
-    B->work_begin[B->count] = (int)w.size();
-    if (B->d_work) cudaFree(B->d_work);
-    B->d_work = nullptr;
-    BX_CUDA(cudaMalloc((void **)&B->d_work, w.size() * sizeof(int4)), "work list allocation");
-    BX_CUDA(cudaMemcpy(B->d_work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice),
-            "work list upload");
     return CX_OK;
 }
 
@@ -142,17 +158,40 @@ cudaError_t one_step(cx_batch *B, int i0, int i1, int parity)
 
 int next_parity(const cx_batch *B, int parity) { return B->scheme == CX_SCHEME_HEUN ? parity : parity ^ 1; }
 
-// Capture graph_steps steps of group gi starting at `parity` (an Euler chunk
-// is even, so it ends at the parity it started from).
-int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out)
+// One pass over instances [i0, i1) starting at *parity: two stages when the
+// depth is 2 (two Euler steps if at least two are left, or one Heun step),
+// else one step.  Sets *steps to the time steps taken and *parity to the
+// parity after them.
+cudaError_t one_pass(cx_batch *B, int i0, int i1, int *parity, int64_t left, int *steps)
+{
+    const bool heun = B->scheme == CX_SCHEME_HEUN;
+    if (B->time_block == 2 && (heun || left >= 2)) {
+        const int w0 = B->work2_begin[i0], w1 = B->work2_begin[i1];
+        const cudaError_t e = cx::launch_batch_fused(B->prec, B->law, B->mob, B->d_inst,
+                                                     B->d_work2 + w0, w1 - w0, *parity, B->rows,
+                                                     heun ? 1 : 0, B->stream);
+        *parity ^= 1;
+        *steps = heun ? 1 : 2;
+        return e;
+    }
+    const cudaError_t e = one_step(B, i0, i1, *parity);
+    *parity = next_parity(B, *parity);
+    *steps = 1;
+    return e;
+}
+
+// Capture graph_steps steps of group gi starting at `parity`; *end gets the
+// parity after them (a graph is kept per starting parity).
+int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out, int *end)
 {
     cudaGraph_t graph = nullptr;
     BX_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     cudaError_t e = cudaSuccess;
     int par = parity;
-    for (int s = 0; s < B->graph_steps && e == cudaSuccess; ++s) {
-        e = one_step(B, B->group_first[gi], B->group_first[gi + 1], par);
-        par = next_parity(B, par);
+    for (int64_t left = B->graph_steps; left > 0 && e == cudaSuccess;) {
+        int taken = 1;
+        e = one_pass(B, B->group_first[gi], B->group_first[gi + 1], &par, left, &taken);
+        left -= taken;
     }
     cudaError_t e2 = cudaStreamEndCapture(B->stream, &graph);
     if (e != cudaSuccess) return bcuda(e, "launch during graph capture");
@@ -160,6 +199,7 @@ int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out)
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bcuda(e, "graph instantiate");
+    *end = par;
     return CX_OK;
 }
 
@@ -232,6 +272,7 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
     B->law = params[0].chemo_law;
     B->mob = params[0].mobility;
     B->scheme = params[0].scheme;
+    B->time_block = B->prec == CX_PREC_F32 ? 2 : 1;  // as a single grid
     B->elem = B->prec == CX_PREC_F64 ? sizeof(double) : sizeof(float);
     B->g.assign(grids, grids + count);
     B->p.assign(params, params + count);
@@ -359,6 +400,27 @@ int cx_batch_get_tuning(cx_batch *B, int32_t *tile_rows, int32_t *graph_steps, i
     return CX_OK;
 }
 
+int cx_batch_set_time_block(cx_batch *B, int32_t stages)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (stages != 1 && stages != 2)
+        return bfail(CX_ERR_INVALID_ARG, "time block: must be 1 or 2 stages per pass");
+    BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before retuning");
+    drop_graphs(B);
+    B->time_block = stages;
+    return CX_OK;
+}
+
+int cx_batch_get_time_block(cx_batch *B, int32_t *stages)
+{
+    int rc = check_batch(B);
+    if (rc) return rc;
+    if (!stages) return bfail(CX_ERR_INVALID_ARG, "stages must not be NULL");
+    *stages = B->time_block;
+    return CX_OK;
+}
+
 int cx_batch_step(cx_batch *B, int64_t n_steps)
 {
     cx::NvtxRange range("cx_batch_step");
@@ -367,9 +429,12 @@ int cx_batch_step(cx_batch *B, int64_t n_steps)
     if (n_steps < 0) return bfail(CX_ERR_INVALID_ARG, "n_steps < 0");
     if (n_steps == 0) return CX_OK;
     const int ngroups = (int)B->group_first.size() - 1;
-    if (B->graph_steps > 0 && (int)B->gexec.size() != ngroups) {
+    if (B->graph_steps > 0 && (int)B->gexec[0].size() != ngroups) {
         drop_graphs(B);
-        B->gexec.assign(ngroups, nullptr);
+        for (int p = 0; p < 2; ++p) {
+            B->gexec[p].assign(ngroups, nullptr);
+            B->gend[p].assign(ngroups, 0);
+        }
     }
     int end_parity = B->cur;
     for (int gi = 0; gi < ngroups; ++gi) {
@@ -381,27 +446,21 @@ int cx_batch_step(cx_batch *B, int64_t n_steps)
             if (rc) return rc;
             continue;
         }
-        if (B->graph_steps > 0 && left >= B->graph_steps) {
-            // Euler graphs start at parity 0 (and, being even, end there)
-            if (B->scheme == CX_SCHEME_EULER && par == 1) {
-                BX_CUDA(one_step(B, i0, i1, par), "batch step launch");
-                par = 0;
-                --left;
-            }
-            if (left >= B->graph_steps) {
-                if (!B->gexec[gi]) {
-                    rc = capture_group(B, gi, par, &B->gexec[gi]);
+        if (B->graph_steps > 0) {
+            while (left >= B->graph_steps) {
+                if (!B->gexec[par][gi]) {
+                    rc = capture_group(B, gi, par, &B->gexec[par][gi], &B->gend[par][gi]);
                     if (rc) return rc;
                 }
-                while (left >= B->graph_steps) {
-                    BX_CUDA(cudaGraphLaunch(B->gexec[gi], B->stream), "graph launch");
-                    left -= B->graph_steps;
-                }
+                BX_CUDA(cudaGraphLaunch(B->gexec[par][gi], B->stream), "graph launch");
+                left -= B->graph_steps;
+                par = B->gend[par][gi];
             }
         }
-        for (; left > 0; --left) {
-            BX_CUDA(one_step(B, i0, i1, par), "batch step launch");
-            par = next_parity(B, par);
+        while (left > 0) {
+            int taken = 1;
+            BX_CUDA(one_pass(B, i0, i1, &par, left, &taken), "batch step launch");
+            left -= taken;
         }
         end_parity = par;
     }

@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<T, NOISE, HEUN>())
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xb = blockIdx.x * kFusedBlockCols;  // first written column of the block
+    // warps share nothing, so a warp whose written columns all lie past the
+    // row's end (ragged last tile) leaves at once
+    if (xb + warp * kFusedCols >= nx) return;
     const int x0 = xb + warp * kFusedCols - kCells + lane * kCells;
     const int j0 = blockIdx.y * rows;
     const int jend = min(j0 + rows, ny);

@@ -109,6 +109,10 @@ void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void 
                int nx, int ny, long long pitch, const Coef &k, double bth);
 cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, const int4 *work,
                               int nwork, int parity, int rows, int stage, cudaStream_t st);
+// Two stages per pass over a 480-column work list: reads u(parity), writes
+// u(parity^1); heun 0: two Euler steps, 1: one Heun step.
+cudaError_t launch_batch_fused(int prec, int law, int mob, const void *inst, const int4 *work,
+                               int nwork, int parity, int rows, int heun, cudaStream_t st);
 cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,
                               int parity, double *part, double *out, cudaStream_t st);
 // nsteps steps of the work items [0, nwork) in one cooperative launch with

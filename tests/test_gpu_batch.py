@@ -47,7 +47,9 @@ def single_runs(cx, sp, steps, dtype):
 @pytest.mark.parametrize("prec,scheme", [(1, 0), (0, 0), (1, 1)])
 @pytest.mark.parametrize("tuning", [(32, 0, 0, 0), (8, 10, 0, 0), (64, 64, 0, 0),
                                     (16, 12, 400_000, 0), (8, 0, 400_000, 7), (4, 0, 0, 50),
-                                    (32, 0, 0, 1)])
+                                    (32, 0, 0, 1), (32, 0, 0, 0, 1), (8, 10, 0, 0, 1),
+                                    (64, 64, 0, 0, 2), (16, 12, 400_000, 0, 2), (5, 6, 0, 0, 2),
+                                    (3, 0, 0, 0, 2)])
 def test_batch_matches_single_grids_bitwise(cx, prec, scheme, tuning):
     sp = specs(prec, scheme)
     dtype = np.float32 if prec == 1 else np.float64
@@ -118,6 +120,18 @@ def test_resident_barrier_timeout_is_reported(cx, monkeypatch):
         bt2.tune(8, 0, 0, 10)
         bt2.step(20)
         assert bt2.diagnostics()[0]["finite"] == 1
+
+
+def test_batch_time_block_default_and_validation(cx):
+    for prec, default in ((1, 2), (0, 1)):
+        with cx.Batch(specs(prec, 0, sizes=[(64, 48), (7, 5)])) as bt:
+            assert cx.cx_batch_get_time_block(bt.h) == default
+            for bad in (0, 3):
+                with pytest.raises(cx.CxError) as e:
+                    cx.cx_batch_set_time_block(bt.h, bad)
+                assert e.value.code == cx.CX_ERR_INVALID_ARG
+            cx.cx_batch_set_time_block(bt.h, 3 - default)
+            assert cx.cx_batch_get_time_block(bt.h) == 3 - default
 
 
 def test_single_grid_tile_rows_do_not_change_results(cx):
