@@ -263,9 +263,10 @@ def test_field_io_converts_precision(cx):
 
 
 # ---------------------------------------------------------------------------
-# The 16384^2 FP32 workload, in the launch configuration the benchmark times:
-# the oracle checks one step on sampled windows (corners, edges, interior,
-# the ragged end of a block) from the same FP32 state.
+# The 16384^2 FP32 workload, in the launch configuration the benchmark times
+# (two Euler steps per pass): the oracle checks one pass, two steps, on
+# sampled windows (corners, edges, interior, the ragged ends of blocks) from
+# the same FP32 state.
 
 def _envelope_series(cx, cfg, prec, steps, samples):
     with make_sim(cx, cfg, prec)[0] as sim:
@@ -320,22 +321,23 @@ def test_error_table_fp32_fp64_against_oracle(cx, n, steps):
     assert max(errs[0]) <= TOL64 and max(errs[1]) <= TOL32
 
 
-def _window_error(cfg, dt, s, b0, n0, b1, n1, windows, size=40):
+def _window_error(cfg, dt, s, b0, n0, b1, n1, windows, size=40, steps=2):
     nx, ny = cfg["nx"], cfg["ny"]
     worst = 0.0
     for (x0, y0) in windows:
         xa, ya = max(x0, 0), max(y0, 0)
         xb, yb = min(x0 + size, nx), min(y0 + size, ny)
         sub = lambda a: a[ya:yb, xa:xb].astype(np.float64)
-        ob, on = oracle.step(sub(s), sub(b0), sub(n0), dx=cfg["dx"], dt=dt, Dn=cfg["Dn"],
-                             theta=cfg["theta"], chi0=cfg["chi0"])
+        ob, on, _ = oracle.run(sub(s), sub(b0), sub(n0), steps, dx=cfg["dx"], dt=dt,
+                               Dn=cfg["Dn"], theta=cfg["theta"], chi0=cfg["chi0"])
         # the window's own edges are walls for the oracle: compare only cells
-        # whose four faces lie inside the window or on the true domain wall
+        # whose dependence cone (`steps` cells) lies inside the window or
+        # reaches only the true domain wall
         m = np.ones(ob.shape, bool)
-        if xa > 0: m[:, 0] = False
-        if xb < nx: m[:, -1] = False
-        if ya > 0: m[0, :] = False
-        if yb < ny: m[-1, :] = False
+        if xa > 0: m[:, :steps] = False
+        if xb < nx: m[:, -steps:] = False
+        if ya > 0: m[:steps, :] = False
+        if yb < ny: m[-steps:, :] = False
         eb = np.abs(ob - b1[ya:yb, xa:xb])[m].max()
         en = np.abs(on - n1[ya:yb, xa:xb])[m].max()
         worst = max(worst, eb, en)
@@ -347,9 +349,11 @@ def test_full_size_fp32_sampled_windows(cx):
     nx, ny = cfg["nx"], cfg["ny"]
     c = nx // 2
     edges = [(0, 0), (nx - 40, 0), (0, ny - 40), (nx - 40, ny - 40), (c - 20, 0), (0, c - 20),
-             (511 - 10, c + 30), (4095, 31 * 32 - 5), (nx - 513, ny - 33)]
+             (511 - 10, c + 30), (4095, 31 * 32 - 5), (nx - 513, ny - 33),
+             (480 - 20, 64 * 7 - 20), (119 - 20, c), (34 * 480 - 20, ny - 70)]
     centre = [(c - 20, c - 20), (c - 60, c - 3), (c + 5, c - 50), (c - 45, c + 10)]
     with make_sim(cx, cfg, cx.CX_PREC_F32)[0] as sim:
+        assert cx.cx_get_time_block(sim.h) == 2  # the benchmark's configuration
         dt = cx.cx_get_time(sim.h)[2]
         d0 = sim.diagnostics()
         # phase 1: the inoculum after 200 steps (the colony is near the centre)
@@ -357,23 +361,23 @@ def test_full_size_fp32_sampled_windows(cx):
         s = sim.field(cx.CX_FIELD_SIGMA, np.float32)
         b0 = sim.field(cx.CX_FIELD_B, np.float32)
         n0 = sim.field(cx.CX_FIELD_N, np.float32)
-        sim.step(1)
+        sim.step(2)
         b1 = sim.field(cx.CX_FIELD_B, np.float32)
         n1 = sim.field(cx.CX_FIELD_N, np.float32)
         d1 = sim.diagnostics()
         assert abs(d1["invariant"] - d0["invariant"]) <= 1e-6 * d0["invariant"]
         assert d1["min_b"] >= 0 and d1["min_n"] >= 0 and d1["finite"] == 1
-        assert _window_error(cfg, dt, s, b0, n0, b1, n1, centre + edges) <= 1e-6
+        assert _window_error(cfg, dt, s, b0, n0, b1, n1, centre + edges) <= 2e-6
         # phase 2: seeded random fields everywhere, so every window is busy
         rng = np.random.default_rng(2024)
         b0 = (0.05 + 0.5 * rng.random((ny, nx), dtype=np.float32)).astype(np.float32)
         n0 = (0.05 + 0.4 * rng.random((ny, nx), dtype=np.float32)).astype(np.float32)
         sim.set_field(cx.CX_FIELD_B, b0)
         sim.set_field(cx.CX_FIELD_N, n0)
-        sim.step(1)
+        sim.step(2)
         b1 = sim.field(cx.CX_FIELD_B, np.float32)
         n1 = sim.field(cx.CX_FIELD_N, np.float32)
-    assert _window_error(cfg, dt, s, b0, n0, b1, n1, centre + edges) <= 2e-6
+    assert _window_error(cfg, dt, s, b0, n0, b1, n1, centre + edges) <= 4e-6
 
 
 # ---------------------------------------------------------------------------
