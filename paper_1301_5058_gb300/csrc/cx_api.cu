@@ -281,15 +281,18 @@ int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit)
 }
 
 // Automatic tile height: 32 rows per tile for one stage per pass, 64 for two
-// (the fused march's first and last tile rows repeat work of the neighbour
-// tiles), or fewer so that a small grid still launches about four tiles per
-// SM (152 SMs) instead of a handful of long, latency-bound marches.
+// (the two-stage march's first and last tile rows repeat work of the
+// neighbour tiles), or fewer so that a smaller grid still launches about four
+// tiles per SM (eight with two stages, whose blocks hold fewer warps per SM)
+// instead of a handful of long, latency-bound marches.
 static int auto_tile_rows(const cx_ctx *c)
 {
-    const long long cols = c->time_block == 2 ? 480 : 512;
-    const long long cap = c->time_block == 2 ? 64 : 32;
+    const bool two = c->time_block == 2;
+    const long long cols = two ? 480 : 512;
+    const long long cap = two ? 64 : 32;
+    const long long per_sm = two ? 8 : 4;
     const long long tiles_x = ((long long)c->g.nx + cols - 1) / cols;
-    long long rows = ((long long)c->g.ny * tiles_x + 4 * 152 - 1) / (4 * 152);
+    long long rows = ((long long)c->g.ny * tiles_x + per_sm * 152 - 1) / (per_sm * 152);
     rows = rows < 1 ? 1 : (rows > cap ? cap : rows);
     while (((long long)c->g.ny + rows - 1) / rows > 65535) ++rows;
     return (int)rows;

@@ -135,11 +135,11 @@ def test_automatic_tile_height_follows_the_depth(cx):
         cx.cx_set_time_block(sim.h, 2)
         assert cx.cx_get_tile_rows(sim.h) == 64
     with cx.Sim(4096, 4096, 1.0, seed=0, **params) as sim:
-        assert cx.cx_get_tile_rows(sim.h) == -(-4096 * 9 // 608)  # 9 tiles of 480 columns
+        assert cx.cx_get_tile_rows(sim.h) == -(-4096 * 9 // (8 * 152))  # 9 tiles of 480 columns
         cx.cx_set_tile_rows(sim.h, 17)
         assert cx.cx_get_tile_rows(sim.h) == 17
         cx.cx_set_tile_rows(sim.h, 0)
-        assert cx.cx_get_tile_rows(sim.h) == 61
+        assert cx.cx_get_tile_rows(sim.h) == 31
 
 
 def test_autotuner_picks_depth_and_height(cx, tmp_path, monkeypatch):

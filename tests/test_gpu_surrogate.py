@@ -102,6 +102,9 @@ def test_validated_throughput_and_active_sweep_small(cx):
     assert out["batched_solver_points_per_hour"] > out["single_instance_points_per_hour"] > 0
     assert 0.0 <= out["accepted_fraction"] <= 1.0
     assert np.isfinite(out["heldout_rel_error_median_all"])
+    assert out["campaign_points"] == 128 * 5 and out["campaign_points_per_hour"] > 0
+    noise = surrogate.label_noise(side=64, steps=400, points=8, seeds=3)
+    assert noise["moving_points"] <= 8 and 0.0 <= noise["runs_within_1pct_of_point_mean"] <= 1.0
     res = surrogate.active_sweep(rounds=2, per_round=16, first=32, pool=256, seed=1,
                                  label_kw=dict(side=64, steps=400, samples=8),
                                  train_kw=dict(steps=300, lr=2e-3, batch=32))
