@@ -402,7 +402,7 @@ def main():
         roofline = dict(hbm, alu_fp32=alu)
         if args.time_block == 2:
             roofline["limiter"] = ("instruction issue: two stages per pass halve the HBM bytes "
-                                   "per cell-update, and the pass then issues about 72 thread "
+                                   "per cell-update, and the pass then issues about 64 thread "
                                    "instructions per cell-update (ncu)")
     out = {
         "metric": "grid-cell updates/s",

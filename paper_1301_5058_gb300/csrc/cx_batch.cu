@@ -173,14 +173,11 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
 
 // Two stages per pass (two Euler steps, or one Heun step) of one tile of the
 // 480-column work list: reads u(parity), writes u(parity^1).  Register
-// budget as the single-grid two-stage pass (96 registers for FP32 Euler).
-template <typename T, bool HEUN> constexpr int batch_fused_min_blocks()
-{
-    return sizeof(T) == 4 ? (HEUN ? 4 : 5) : 2;
-}
+// budget as the single-grid two-stage pass (128 registers in FP32).
+template <typename T> constexpr int batch_fused_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T, int LAW, int MOB, bool HEUN>
-__global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T, HEUN>())
+__global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
     batch_fused_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                        int parity, int rows)
 {

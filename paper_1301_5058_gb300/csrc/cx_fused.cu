@@ -18,21 +18,20 @@ namespace {
 
 using namespace stencil;
 
-// Resident blocks per SM the register budget is sized for.  FP32 Euler with
-// a static sigma field: 5 (at most 96 registers; the march waits on loads,
-// so 20 warps per SM beat 16 warps with more registers); FP32 with per-step
-// noise or Heun: 4 (Philox and the start-of-step state need the registers);
-// FP64: 2 (bound by the FP64 pipe, not by occupancy).
+// Resident blocks per SM the register budget is sized for: FP32 4 (at most
+// 128 registers; with 96 the march's steady state spills, and 5 blocks per
+// SM ran 6 % slower than 4), FP64 2 (bound by the FP64 pipe, not by
+// occupancy).
 #ifndef CX_FUSED_MIN_BLOCKS_F32
-#define CX_FUSED_MIN_BLOCKS_F32 5
+#define CX_FUSED_MIN_BLOCKS_F32 4
 #endif
-template <typename T, int NOISE, bool HEUN> constexpr int fused_min_blocks()
+template <typename T> constexpr int fused_min_blocks()
 {
-    return sizeof(T) == 4 ? (NOISE == 0 && !HEUN ? CX_FUSED_MIN_BLOCKS_F32 : 4) : 2;
+    return sizeof(T) == 4 ? CX_FUSED_MIN_BLOCKS_F32 : 2;
 }
 
 template <typename T, int LAW, int MOB, int NOISE, bool HEUN>
-__global__ void __launch_bounds__(kThreads, fused_min_blocks<T, NOISE, HEUN>())
+__global__ void __launch_bounds__(kThreads, fused_min_blocks<T>())
     fused_kernel(Ptrs<T> P, int nx, int ny, long long pitch, KV<P2<T>> k, NoiseT<T> nz1,
                  NoiseT<T> nz2, int rows)
 {

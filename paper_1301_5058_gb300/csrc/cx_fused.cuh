@@ -19,6 +19,8 @@
 // two passes it replaces.
 #pragma once
 
+#include <type_traits>
+
 #include "cx_stencil.cuh"
 
 namespace cx {
@@ -87,9 +89,13 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
 
     const int rfirst = DIR > 0 ? j0 - 2 : jend + 1;
     const int iters = (jend - j0) + 4;
-    for (int p = 0; p < iters; ++p) {
+    // One iteration.  In the steady state (STEADY: from the fifth iteration
+    // on, in a tile whose rows j0-2 .. jend+1 all lie inside the grid) every
+    // row is in the grid and both stages run, so the tests drop out.
+    auto body = [&](int p, auto steady) {
+        constexpr bool STEADY = decltype(steady)::value;
         const int r = rfirst + DIR * p;
-        const bool in_r = r >= 0 && r < ny;  // uniform across the block
+        const bool in_r = STEADY || (r >= 0 && r < ny);  // uniform across the block
         Cells<T> br = zero_cells<T>(), nr = zero_cells<T>(), sr = zero_cells<T>();
         if (in_r) {
             const long long off = (long long)r * pitch + xv;
@@ -100,8 +106,9 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
 
         // first-stage faces between q and r (a wall past the grid), then the
         // first stage of row q
-        const YFaces<T> yA0 = (in_q && in_r) ? yfaces(s0, n0, b0, sr, nr, br) : zero_yfaces<T>();
-        const bool do1 = in_q && p >= 2;
+        const bool both = STEADY || (in_q && in_r);
+        const YFaces<T> yA0 = both ? yfaces(s0, n0, b0, sr, nr, br) : zero_yfaces<T>();
+        const bool do1 = STEADY || (in_q && p >= 2);
         Cells<T> b1q = zero_cells<T>(), n1q = zero_cells<T>();
         T ls0 = T(0), rs0 = T(0);
         if (do1) {
@@ -116,9 +123,9 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         if (!kSameSigma) s2q = do1 ? gen_sigma(nz2, r - DIR) : zero_cells<T>();
 
         // second-stage faces between o and q, then the second stage of row o
-        const YFaces<T> yA1 =
-            (do1 && in_o) ? yfaces(s1, n1, b1, s2q, n1q, b1q) : zero_yfaces<T>();
-        if (p >= 4) {
+        const bool have_o = STEADY || (do1 && in_o);
+        const YFaces<T> yA1 = have_o ? yfaces(s1, n1, b1, s2q, n1q, b1q) : zero_yfaces<T>();
+        if (STEADY || p >= 4) {
             const int o = r - 2 * DIR;
             if (!kSameSigma) {
                 ls1 = __shfl_up_sync(kFull, s1.O.y, 1);
@@ -169,6 +176,17 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         }
         in_o = do1;
         in_q = in_r;
+    };
+
+    const int head = iters < 4 ? iters : 4;
+    int p = 0;
+    for (; p < head; ++p) body(p, std::false_type{});
+    // uniform across the block: the rows the remaining iterations load
+    const bool rows_inside = DIR > 0 ? jend + 1 < ny : j0 >= 2;
+    if (rows_inside) {
+        for (; p < iters; ++p) body(p, std::true_type{});
+    } else {
+        for (; p < iters; ++p) body(p, std::false_type{});
     }
 }
 
