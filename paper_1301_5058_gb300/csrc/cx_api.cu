@@ -462,6 +462,15 @@ static int check_io(cx_ctx *c, int32_t which, const void *host, int32_t dtype, s
     return CX_OK;
 }
 
+// Rows of `row` bytes between a pitched and a packed array: one linear copy
+// when the pitch equals the row (no padding), else a 2D copy.
+static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t row,
+                             size_t rows, cudaMemcpyKind kind, cudaStream_t st)
+{
+    if (dpitch == row && spitch == row) return cudaMemcpyAsync(dst, src, row * rows, kind, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, rows, kind, st);
+}
+
 int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t count)
 {
     int rc = check_io(c, which, host, dtype, count);
@@ -473,7 +482,7 @@ int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t cou
         CX_CUDA(fill_sigma(c, c->step), "sigma regeneration");
     CX_CUDA(cudaStreamSynchronize(c->stream), "synchronize before field read");
     if (dtype == state_dtype) {
-        CX_CUDA(cudaMemcpy2DAsync(host, row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
+        CX_CUDA(copy_rows(host, row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
                                   c->g.ny, cudaMemcpyDeviceToHost, c->stream),
                 "field copy to host");
         CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
@@ -482,7 +491,7 @@ int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t cou
     // precision change: copy in the state type, widen or narrow on the host
     std::vector<unsigned char> tmp;
     try { tmp.resize(count * c->elem); } catch (...) { return fail(CX_ERR_OOM, "host staging"); }
-    CX_CUDA(cudaMemcpy2DAsync(tmp.data(), row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
+    CX_CUDA(copy_rows(tmp.data(), row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
                               c->g.ny, cudaMemcpyDeviceToHost, c->stream),
             "field copy to host");
     CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
@@ -522,8 +531,8 @@ int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size
         }
         src = tmp.data();
     }
-    CX_CUDA(cudaMemcpy2DAsync(field_ptr(c, which), (size_t)c->pitch * c->elem, src, row, row,
-                              c->g.ny, cudaMemcpyHostToDevice, c->stream),
+    CX_CUDA(copy_rows(field_ptr(c, which), (size_t)c->pitch * c->elem, src, row, row, c->g.ny,
+                      cudaMemcpyHostToDevice, c->stream),
             "field copy to device");
     CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
     return CX_OK;
