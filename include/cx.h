@@ -14,8 +14,8 @@
  *   sigma  = sigma0 (1 + a Delta)                                (Eq. CoefCrsDif)
  *
  * on an nx*ny cell-centred grid of spacing dx with no-flux walls
- * (Eq. bconds), initial data n = n0 and b = bM exp(-r^2/r0sq) (Eq. inicond,
- * Eq. inibacexp), by explicit finite volumes (face fluxes with arithmetic
+ * (Eq. bconds), initial data n = n0 and b = bM exp(-r^2/r0sq), cut to zero
+ * where r^2/r0sq > 40 (Eq. inicond, Eq. inibacexp), by explicit finite volumes (face fluxes with arithmetic
  * face means) and forward Euler or Heun time stepping (Sec. 3).
  *
  * Conventions for every call:
@@ -96,7 +96,8 @@ typedef struct {
     double Dn;          /* nutrient diffusivity, >= 0 */
     double theta;       /* conversion factor, >= 0 */
     double bM;          /* inoculum peak (Eq. inibacexp) */
-    double r0sq;        /* inoculum width: b = bM exp(-r^2 / r0sq), > 0 */
+    double r0sq;        /* inoculum width: b = bM exp(-r^2 / r0sq) where
+                           r^2 / r0sq <= 40, else 0 (compact support), > 0 */
     double dt;          /* time step; 0 selects cfl_frac * cx_dt_limit() */
     double cfl_frac;    /* fraction of the limit used when dt == 0, (0, 1] */
     double b_threshold; /* envelope level for r_env; <= 0 selects 0.1 theta n0 */

@@ -146,7 +146,11 @@ void orc_sigma_field(int nx, int ny, uint64_t seed, uint64_t step,
 }
 
 /* Initial state (Eq. inicond, Eq. inibacexp): n = n0 everywhere and a
- * Gaussian inoculum b = bM exp(-r^2 / r0sq) centred on the domain. */
+ * Gaussian inoculum b = bM exp(-r^2 / r0sq) centred on the domain, read as
+ * cut to zero where r^2 / r0sq > 40 (a real inoculum has compact support;
+ * the cut changes its mass by less than e^-40 and keeps every nonzero value
+ * a normal FP32 number, so an FP32 and an FP64 state start alike instead of
+ * differing wherever FP32 underflows). */
 void orc_initial_state(int nx, int ny, double dx, double n0, double bM,
                        double r0sq, double *b, double *n)
 {
@@ -156,7 +160,8 @@ void orc_initial_state(int nx, int ny, double dx, double n0, double bM,
             double y = ((double)j + 0.5 - 0.5 * (double)ny) * dx;
             double r2 = x * x + y * y;
             size_t p = (size_t)j * (size_t)nx + (size_t)i;
-            b[p] = bM * exp(-r2 / r0sq);
+            double q = -r2 / r0sq;
+            b[p] = q < -40.0 ? 0.0 : bM * exp(q);
             n[p] = n0;
         }
 }

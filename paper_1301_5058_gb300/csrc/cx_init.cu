@@ -51,9 +51,10 @@ __global__ void initial_state_kernel(T *__restrict__ b, T *__restrict__ n, int n
         const double y = __dmul_rn((double)j + 0.5 - 0.5 * (double)ny, dx);
         const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
         const double q = __ddiv_rn(-r2, r0sq);
-        // exp(q) is exactly 0 in FP64 below about -745.13; skipping the call
-        // there changes no value and spares most cells of a large grid
-        const double e = q < -800.0 ? 0.0 : exp(q);
+        // the inoculum is cut to zero where r^2 / r0sq > 40 (compact support:
+        // an FP32 and an FP64 state start alike; the mass changes by less
+        // than e^-40), which also spares the exp of most cells of a grid
+        const double e = q < -40.0 ? 0.0 : exp(q);
         b[(long long)j * pitch + i] = (T)__dmul_rn(bM, e);
         n[(long long)j * pitch + i] = (T)n0;
     }
