@@ -95,26 +95,26 @@ double orc_noise_delta(uint64_t seed, uint64_t idx, uint64_t step, int dist)
 }
 
 /* FP32 recipe, used when the state is held in FP32 and sigma is redrawn
- * every step: one Philox block serves the two cells of a pair, block
- * counter (q lo, q hi, step lo, step hi) with q = idx >> 1, and cell idx
- * takes words w[2h], w[2h+1] with h = idx & 1.  With the 24-bit integers
- * j_a = w[2h] >> 8, j_b = w[2h+1] >> 8,
- *   dist 0:  Delta = (2 j_a - 2^24) 2^-24,   dist 1:  Delta = (j_a + j_b - 2^24) 2^-24,
+ * every step: one Philox block serves four consecutive cells, block counter
+ * (q lo, q hi, step lo, step hi) with q = idx >> 2, and cell idx takes word
+ * w[h], h = idx & 3, as two 16-bit integers j_a = w[h] >> 16 and
+ * j_b = w[h] & 0xffff:
+ *   dist 0:  Delta = (2 j_a - 2^16) 2^-16,   dist 1:  Delta = (j_a + j_b - 2^16) 2^-16,
  * exact in float, then sigma = sigma0 (1 + a Delta) with each float
  * operation rounded on its own. */
 float orc_noise_sigma_f32(uint64_t seed, uint64_t idx, uint64_t step, int dist,
                           float sigma0, float amp)
 {
-    uint64_t q = idx >> 1;
-    int h = (int)(idx & 1);
+    uint64_t q = idx >> 2;
+    int h = (int)(idx & 3);
     uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32),
                        (uint32_t)step, (uint32_t)(step >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
-    int32_t ja = (int32_t)(w[2 * h] >> 8), jb = (int32_t)(w[2 * h + 1] >> 8);
-    int32_t num = (dist == 0) ? (2 * ja - (1 << 24)) : (ja + jb - (1 << 24));
-    float d = (float)num * 0x1p-24f;
+    int32_t ja = (int32_t)(w[h] >> 16), jb = (int32_t)(w[h] & 0xffffu);
+    int32_t num = (dist == 0) ? (2 * ja - (1 << 16)) : (ja + jb - (1 << 16));
+    float d = (float)num * 0x1p-16f;
     float t = amp * d;
     float s = 1.0f + t;
     return sigma0 * s;

@@ -3,7 +3,8 @@
 // sigma = sigma0 (1 + a Delta) (Eq. CoefCrsDif) with Delta drawn per cell
 // from Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random
 // numbers: as easy as 1, 2, 3", SC'11), counter (cell index lo, hi, time
-// step lo, hi), key (seed lo, hi).  Delta is formed exactly in integers and
+// step lo, hi) -- or (cell index / 4, step) for the FP32 recipe -- key
+// (seed lo, hi).  Delta is formed exactly in integers and
 // the products are rounded one at a time (no fused multiply-add), so the
 // field is bit-identical to any other IEEE implementation of the same
 // definition.  Two recipes exist (cx_philox.cuh): the FP64 one (static
@@ -11,7 +12,8 @@
 // FP32 one (per-step noise of an FP32 state).
 //
 // Initial state (Eq. inicond, Eq. inibacexp): n = n0, b = bM exp(-r^2/r0sq)
-// with r the distance of the cell centre from the domain centre.
+// with r the distance of the cell centre from the domain centre, cut to
+// zero where r^2/r0sq > 40.
 #include "cx_internal.h"
 #include "cx_philox.cuh"
 

@@ -57,38 +57,38 @@ __device__ __forceinline__ double sigma_f64(uint64_t seed, uint64_t idx, uint64_
 
 // FP32 recipe, for an FP32 state whose sigma is redrawn every step (GB300's
 // FP64 pipe is too slow to run the FP64 recipe per cell per step).  One
-// Philox block serves the two cells of a pair: counter (q lo, q hi, step lo,
-// step hi) with q = idx >> 1; cell idx takes words w[2h], w[2h+1] with
-// h = idx & 1.  With the 24-bit integers j_a = w[2h] >> 8, j_b = w[2h+1] >> 8,
-//   dist 0:  Delta = (2 j_a - 2^24) 2^-24,   dist 1:  Delta = (j_a + j_b - 2^24) 2^-24,
+// Philox block serves four consecutive cells: counter (q lo, q hi, step lo,
+// step hi) with q = idx >> 2; cell idx takes word w[h], h = idx & 3, as the
+// 16-bit integers j_a = w[h] >> 16, j_b = w[h] & 0xffff:
+//   dist 0:  Delta = (2 j_a - 2^16) 2^-16,   dist 1:  Delta = (j_a + j_b - 2^16) 2^-16,
 // exact in FP32, then sigma0 (1 + a Delta) with each operation rounded on
 // its own.
-__device__ __forceinline__ float sigma_from_words(uint32_t wa, uint32_t wb, int dist, float sigma0,
-                                                  float amp)
+__device__ __forceinline__ float sigma_from_word(uint32_t w, int dist, float sigma0, float amp)
 {
-    const int ja = (int)(wa >> 8), jb = (int)(wb >> 8);
-    const int num = dist == 0 ? 2 * ja - (1 << 24) : ja + jb - (1 << 24);
-    const float d = (float)num * 0x1p-24f;
+    const int ja = (int)(w >> 16), jb = (int)(w & 0xffffu);
+    const int num = dist == 0 ? 2 * ja - (1 << 16) : ja + jb - (1 << 16);
+    const float d = (float)num * 0x1p-16f;
     return __fmul_rn(sigma0, __fadd_rn(1.0f, __fmul_rn(amp, d)));
 }
 
-// sigma of cells 2q (even) and 2q + 1 (odd).
-__device__ __forceinline__ void sigma_pair_f32(uint64_t seed, uint64_t q, uint64_t step, int dist,
-                                               float sigma0, float amp, float &even, float &odd)
+// the Philox block of cells 4q .. 4q+3
+__device__ __forceinline__ uint4 sigma_block_f32(uint64_t seed, uint64_t q, uint64_t step)
 {
-    const uint4 w = philox4x32_10(
+    return philox4x32_10(
         make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    even = sigma_from_words(w.x, w.y, dist, sigma0, amp);
-    odd = sigma_from_words(w.z, w.w, dist, sigma0, amp);
+}
+
+__device__ __forceinline__ uint32_t block_word(const uint4 &w, int h)
+{
+    return h == 0 ? w.x : h == 1 ? w.y : h == 2 ? w.z : w.w;
 }
 
 __device__ __forceinline__ float sigma_f32(uint64_t seed, uint64_t idx, uint64_t step, int dist,
                                            float sigma0, float amp)
 {
-    float even, odd;
-    sigma_pair_f32(seed, idx >> 1, step, dist, sigma0, amp, even, odd);
-    return (idx & 1) ? odd : even;
+    const uint4 w = sigma_block_f32(seed, idx >> 2, step);
+    return sigma_from_word(block_word(w, (int)(idx & 3)), dist, sigma0, amp);
 }
 
 }  // namespace cx

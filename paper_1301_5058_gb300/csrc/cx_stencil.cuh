@@ -321,19 +321,27 @@ template <> struct NoiseT<float> {
     {
         return sigma_f32(seed, (uint64_t)idx, step, dist, sigma0, amp);
     }
-    // cells idx0 .. idx0+3: two Philox blocks when idx0 is even, three when
-    // it is odd (the parity is the same for all threads of a row)
+    // cells idx0 .. idx0+3: one Philox block when idx0 is a multiple of 4
+    // (always, in rows whose width is), two otherwise (the offset is the same
+    // for all threads of a row)
     __device__ __forceinline__ void four(long long idx0, float (&s)[4]) const
     {
-        const uint64_t q = (uint64_t)idx0 >> 1;
-        if ((idx0 & 1) == 0) {
-            sigma_pair_f32(seed, q, step, dist, sigma0, amp, s[0], s[1]);
-            sigma_pair_f32(seed, q + 1, step, dist, sigma0, amp, s[2], s[3]);
+        const uint64_t q = (uint64_t)idx0 >> 2;
+        const int h = (int)(idx0 & 3);
+        const uint4 w0 = sigma_block_f32(seed, q, step);
+        if (h == 0) {
+            s[0] = sigma_from_word(w0.x, dist, sigma0, amp);
+            s[1] = sigma_from_word(w0.y, dist, sigma0, amp);
+            s[2] = sigma_from_word(w0.z, dist, sigma0, amp);
+            s[3] = sigma_from_word(w0.w, dist, sigma0, amp);
         } else {
-            float unused0, unused1;
-            sigma_pair_f32(seed, q, step, dist, sigma0, amp, unused0, s[0]);
-            sigma_pair_f32(seed, q + 1, step, dist, sigma0, amp, s[1], s[2]);
-            sigma_pair_f32(seed, q + 2, step, dist, sigma0, amp, s[3], unused1);
+            const uint4 w1 = sigma_block_f32(seed, q + 1, step);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int k = h + c;
+                s[c] = sigma_from_word(k < 4 ? block_word(w0, k) : block_word(w1, k - 4), dist,
+                                       sigma0, amp);
+            }
         }
     }
 };

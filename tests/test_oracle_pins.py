@@ -351,23 +351,28 @@ def test_c_bar_monotone_in_chi0():
 
 @pytest.mark.parametrize("dist", [0, 1])
 def test_fp32_noise_recipe_laws_and_pairing(dist):
-    # the FP32 recipe draws a pair of cells from one Philox block: the values
-    # are exact floats, the law is uniform / triangular (KS), the two cells of
-    # a pair are uncorrelated, and a cell's value follows from the block of
-    # its pair (words 2h, 2h+1 of the known-answer-pinned generator)
+    # the FP32 recipe draws four cells from one Philox block (a 32-bit word
+    # each, split into two 16-bit integers): the values lie on the exact
+    # 2^-16 lattice, the law is uniform / triangular (KS), the cells of a
+    # block are uncorrelated, and a cell's value follows from word h of its
+    # block (the known-answer-pinned generator)
     s0, a = 4.0, 0.8
     s32 = oracle.sigma_field_f32(300, 200, 11, s0, a, dist=dist, step=5)
     assert np.all(s32 == s32.astype(np.float32))
     flat = ((s32 / s0 - 1) / a).ravel()
-    pairs = flat[: flat.size // 2 * 2].reshape(-1, 2)
-    rho = np.corrcoef(pairs[:, 0], pairs[:, 1])[0, 1]
-    assert abs(rho) < 5 / math.sqrt(len(pairs))
-    for idx in (0, 1, 12345, 59999):
-        w = oracle.philox4x32_10([idx >> 1, 0, 5, 0], [11, 0])
-        h = idx & 1
-        ja, jb = w[2 * h] >> 8, w[2 * h + 1] >> 8
-        num = 2 * ja - (1 << 24) if dist == 0 else ja + jb - (1 << 24)
-        d = np.float32(num) * np.float32(2.0 ** -24)
+    lattice = flat * 2.0 ** 16
+    assert np.max(np.abs(lattice - np.round(lattice))) < 1e-2   # float rounding of a and s0
+    quads = flat[: flat.size // 4 * 4].reshape(-1, 4)
+    for u in range(4):
+        for v in range(u + 1, 4):
+            rho = np.corrcoef(quads[:, u], quads[:, v])[0, 1]
+            assert abs(rho) < 5 / math.sqrt(len(quads))
+    for idx in (0, 1, 2, 3, 12345, 59999):
+        w = oracle.philox4x32_10([idx >> 2, 0, 5, 0], [11, 0])
+        h = idx & 3
+        ja, jb = w[h] >> 16, w[h] & 0xFFFF
+        num = 2 * ja - (1 << 16) if dist == 0 else ja + jb - (1 << 16)
+        d = np.float32(num) * np.float32(2.0 ** -16)
         ref = np.float32(s0) * (np.float32(1.0) + np.float32(a) * d)
         assert s32.ravel()[idx] == np.float64(ref)
     d = np.sort(flat)
@@ -377,7 +382,7 @@ def test_fp32_noise_recipe_laws_and_pairing(dist):
         F = 0.5 * (1 + d)
     m = d.size
     ks = np.max(np.maximum(np.arange(1, m + 1) / m - F, F - np.arange(m) / m))
-    assert ks < 1.63 / math.sqrt(m) + 1e-6
+    assert ks < 1.63 / math.sqrt(m) + 2.0 ** -15
 
 
 # ---------------------------------------------------------------------------
