@@ -270,6 +270,8 @@ struct cx_mlp {
     double *lrow = nullptr, *loss = nullptr;
     float *dataX = nullptr, *dataT = nullptr;  // training set on the device
     int ndata = 0;
+    double *losses = nullptr;  // per-step losses of a training call, on the device
+    int nlosses = 0;
     long long adam_t = 0;
     cudaStream_t st = nullptr;
 };
@@ -281,7 +283,7 @@ void free_mlp(cx_mlp *m)
     if (!m) return;
     void *ptrs[] = {m->P, m->G, m->M, m->V, m->W2b, m->W2T, m->X, m->T, m->H1f, m->H2, m->Y, m->dY,
                     m->dZ2, m->dH1, m->H1b, m->H1T, m->dZ2b, m->dZ2T, m->lrow, m->loss,
-                    m->dataX, m->dataT};
+                    m->dataX, m->dataT, m->losses};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->st) cudaStreamDestroy(m->st);
@@ -435,9 +437,16 @@ int cx_mlp_train(cx_mlp *m, const float *x, const float *t, int32_t n, int32_t b
     }
     MX_CUDA(cudaMemcpyAsync(m->dataX, x, (size_t)n * NI * 4, cudaMemcpyHostToDevice, m->st), "training set upload");
     MX_CUDA(cudaMemcpyAsync(m->dataT, t, (size_t)n * NO * 4, cudaMemcpyHostToDevice, m->st), "training set upload");
+    // the losses stay on the device until the end, so the host queues every
+    // step without waiting for the GPU
+    if (loss_out && m->nlosses < steps) {
+        if (m->losses) cudaFree(m->losses);
+        m->losses = nullptr;
+        m->nlosses = 0;
+        MX_CUDA(cudaMalloc((void **)&m->losses, (size_t)steps * 8), "loss buffer allocation");
+        m->nlosses = steps;
+    }
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    std::vector<double> losses;
-    if (loss_out) losses.resize(steps);
     const int nbatches = n / batch;
     for (int s = 0; s < steps; ++s) {
         const long long first = (long long)(s % nbatches) * batch;  // cyclic minibatches
@@ -447,11 +456,16 @@ int cx_mlp_train(cx_mlp *m, const float *x, const float *t, int32_t n, int32_t b
         adam<<<(NPARAM + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->M, m->V, NPARAM, lr, b1, b2, eps, c1, c2);
         refresh_w2<<<(H * H + 255) / 256, 256, 0, m->st>>>(m->P, m->W2b, m->W2T);
         MX_CUDA(cudaGetLastError(), "optimiser launch");
-        if (loss_out) MX_CUDA(cudaMemcpyAsync(&losses[s], m->loss, 8, cudaMemcpyDeviceToHost, m->st), "loss download");
+        if (loss_out)
+            MX_CUDA(cudaMemcpyAsync(m->losses + s, m->loss, 8, cudaMemcpyDeviceToDevice, m->st),
+                    "loss record");
     }
+    if (loss_out && steps > 0)
+        MX_CUDA(cudaMemcpyAsync(loss_out, m->losses, (size_t)steps * 8, cudaMemcpyDeviceToHost, m->st),
+                "loss download");
     MX_CUDA(cudaStreamSynchronize(m->st), "training synchronize");
     if (loss_out)
-        for (int s = 0; s < steps; ++s) loss_out[s] = losses[s] / (double)batch;
+        for (int s = 0; s < steps; ++s) loss_out[s] /= (double)batch;
     return CX_OK;
 }
 

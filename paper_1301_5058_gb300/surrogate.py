@@ -232,9 +232,15 @@ class Ensemble:
         self.models = [Surrogate(seed + 17 * k, max_batch) for k in range(members)]
 
     def fit(self, points, velocity, **kw):
+        """Train the members concurrently: each network has its own stream and
+        buffers, and the library calls release the interpreter lock, so the
+        members' small kernels overlap on the GPU; the results do not depend
+        on the interleaving."""
+        from concurrent.futures import ThreadPoolExecutor
         lv = np.log(np.maximum(np.asarray(velocity, np.float64), 1e-12))
         y = np.stack([lv, np.zeros_like(lv)], 1)
-        return [m.fit(points, y, **kw) for m in self.models]
+        with ThreadPoolExecutor(max_workers=len(self.models)) as ex:
+            return list(ex.map(lambda m: m.fit(points, y, **kw), self.models))
 
     def predict(self, points):
         lv = np.stack([m.predict(points)[:, 0] for m in self.models], 0)
