@@ -15,11 +15,11 @@ Surrogate: the MLP of include/cx.h (4 -> 256 -> 256 -> 2, tanh), inputs
 (log n0, chi0, log sigma0, a) mapped affinely from the sweep box to
 [-1, 1]; outputs standardised by the training-set mean and spread.
 
-Active sweep: each round draws a pool of candidates, scores them by how
-close the network puts them to a morphology boundary (a predicted branch
-count near a class boundary, or a steep predicted velocity), sends the best
-`per_round` of them to the solver in one batch, adds the verified labels
-and retrains.
+Active sweep: each round draws a pool of candidates, and the network, its
+branch output trained on the class (branched or not), picks half of
+`per_round` nearest the compact / branched boundary and half where the
+predicted log velocity is steepest (fronts starting to stall); the solver
+verifies them in one batch, the labels are added and the network retrained.
 """
 from __future__ import annotations
 
@@ -155,10 +155,12 @@ class Surrogate:
         self.net.close()
 
 
-def boundary_score(model: Surrogate, pts, level=1.5, eps=0.02):
-    """Higher = closer to a predicted morphology boundary: a branch count
-    near `level` or a steep predicted velocity (finite differences in the
-    normalised inputs)."""
+def boundary_scores(model: Surrogate, pts, level=0.5, eps=0.02, vfloor=1e-3):
+    """Two scores, higher = closer to a predicted morphology boundary: the
+    branch output's closeness to `level` (between compact and branched), and
+    the steepness of the predicted log velocity (finite differences in the
+    normalised inputs; relative changes peak where fronts start to stall)."""
+    logv = lambda p: np.log(np.maximum(model.predict(p)[:, 0], vfloor))
     pred = model.predict(pts)
     near = -np.abs(pred[:, 1] - level)
     X = encode(pts).astype(np.float64)
@@ -166,13 +168,21 @@ def boundary_score(model: Surrogate, pts, level=1.5, eps=0.02):
     for k in range(3):
         step = np.zeros(4)
         step[k] = eps
-        lo, hi = _decode(X - step), _decode(X + step)
-        d = (model.predict(hi)[:, 0] - model.predict(lo)[:, 0]) / (2 * eps)
+        d = (logv(_decode(X + step)) - logv(_decode(X - step))) / (2 * eps)
         grad += d * d
-    g = np.sqrt(grad)
-    gnorm = (g - g.mean()) / (g.std() + 1e-12)
-    nnorm = (near - near.mean()) / (near.std() + 1e-12)
-    return np.maximum(gnorm, nnorm)
+    return near, np.sqrt(grad)
+
+
+def pick_boundary(model: Surrogate, cand, k):
+    """Indices of k candidates: half nearest the compact / branched
+    boundary, half (of the rest) where the predicted log velocity is
+    steepest."""
+    near, steep = boundary_scores(model, cand)
+    kb = k // 2
+    ib = np.argsort(-near)[:kb]
+    rest = np.setdiff1d(np.arange(len(cand)), ib)
+    iv = rest[np.argsort(-steep[rest])[:k - kb]]
+    return np.concatenate([ib, iv])
 
 
 def _decode(X):
@@ -365,8 +375,11 @@ def label_noise(side=256, steps=20000, points=128, seeds=8, seed=0):
 
 def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=None,
                  train_kw=None):
-    """Surrogate-guided sweep.  Returns a dict with every verified point, its
-    labels, and per-round surrogate errors on the newly verified points."""
+    """Surrogate-guided sweep.  Each round the network is retrained on every
+    verified point and picks `per_round` of `pool` candidates (pick_boundary);
+    the solver verifies them.  Returns a dict with every verified point, its
+    labels, and per-round surrogate errors on the newly verified points (the
+    first half of each round's points is the branch-boundary half)."""
     label_kw = label_kw or {}
     train_kw = train_kw or {}
     pts = draw_points(first, seed)
@@ -375,19 +388,55 @@ def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=
     model = Surrogate(seed)
     history = []
     for r in range(rounds):
-        model.fit(P, L, **train_kw)
+        # the branch output is trained on the class (branched or not), so that
+        # 0.5 is its decision boundary; L keeps the counts
+        model.fit(P, np.stack([L[:, 0], (L[:, 1] >= 1).astype(np.float64)], 1), **train_kw)
         cand = draw_points(pool, seed + 1000 + r)
-        score = boundary_score(model, cand)
-        pick = cand[np.argsort(-score)[:per_round]]
+        pick = cand[pick_boundary(model, cand, per_round)]
         pred = model.predict(pick)
         v, b, _ = solver_labels(pick, seed0=len(P), **label_kw)
         rel = np.abs(pred[:, 0] - v) / np.maximum(np.abs(v), 1e-12)
         history.append({"round": r, "median_rel_velocity_error": float(np.median(rel)),
-                        "mean_branch_error": float(np.mean(np.abs(pred[:, 1] - b)))})
+                        "branch_class_accuracy": float(np.mean((pred[:, 1] >= 0.5) == (b >= 1)))})
         P = np.concatenate([P, pick])
         L = np.concatenate([L, np.stack([v, b], 1)])
     model.close()
     return {"points": P, "labels": L, "history": history}
+
+
+def boundary_gain(rounds=3, per_round=128, first=256, pool=8192, seed=0, side=256, steps=20000,
+                  train_steps=6000):
+    """Does the surrogate-guided sweep sample the morphology boundaries?
+    Runs active_sweep, then as many uniformly drawn points through the
+    solver, and compares (a) the share of branched colonies (branch count
+    >= 1) among the branch-boundary picks: most of the box grows compact
+    colonies, so a sampler that concentrates on the compact / branched
+    boundary finds more branched ones than uniform sampling does; (b) the
+    share of slow fronts (velocity below the uniform sample's 10th
+    percentile, near the stall boundary) among the steep-velocity picks."""
+    import json
+    label_kw = dict(side=side, steps=steps)
+    res = active_sweep(rounds=rounds, per_round=per_round, first=first, pool=pool, seed=seed,
+                       label_kw=label_kw, train_kw=dict(steps=train_steps, lr=2e-3, batch=256,
+                                                        decay=3))
+    active_b = res["labels"][first:, 1].reshape(rounds, per_round)
+    branch_half = active_b[:, : per_round // 2]
+    active_v = res["labels"][first:, 0].reshape(rounds, per_round)
+    uni = draw_points(rounds * per_round, seed + 777)
+    uv, ub, _ = solver_labels(uni, seed0=900_000, **label_kw)
+    slow = np.quantile(uv, 0.1)
+    out = {"side": side, "steps_per_point": steps, "first": first, "rounds": rounds,
+           "per_round": per_round,
+           "initial_branched_fraction": float((res["labels"][:first, 1] >= 1).mean()),
+           "uniform_branched_fraction": float((ub >= 1).mean()),
+           "active_branched_fraction": float((active_b >= 1).mean()),
+           "branch_half_branched_fraction": float((branch_half >= 1).mean()),
+           "branch_half_branched_by_round": [float((h >= 1).mean()) for h in branch_half],
+           "velocity_half_slow_fraction": float((active_v[:, per_round // 2:] <= slow).mean()),
+           "uniform_slow_fraction": float((uv <= slow).mean()),
+           "history": res["history"]}
+    print(json.dumps(out))
+    return out
 
 
 if __name__ == "__main__":
@@ -400,6 +449,9 @@ if __name__ == "__main__":
             continue
         if a == "--label-noise":
             mode = label_noise
+            continue
+        if a == "--boundary":
+            mode = boundary_gain
             continue
         k, _, v = a.lstrip("-").partition("=")
         kw[k] = float(v) if "." in v else int(v)
