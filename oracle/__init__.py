@@ -115,9 +115,10 @@ def sigma_field(nx, ny, seed, sigma0, amp, dist=0, step=0) -> np.ndarray:
 
 
 def sigma_field_f32(nx, ny, seed, sigma0, amp, dist=0, step=0) -> np.ndarray:
-    """The FP32 recipe of the same draw (24-bit uniforms, float arithmetic),
-    used by FP32-state runs whose sigma is redrawn every step; returned as
-    float64 (exactly the float values)."""
+    """The FP32 recipe (two 16-bit uniforms per cell from one Philox word,
+    four cells per block, float arithmetic), used by FP32-state runs whose
+    sigma is redrawn every step; returned as float64 (exactly the float
+    values)."""
     s = np.empty((ny, nx), np.float64)
     _load().orc_sigma_field_f32(nx, ny, seed, step, sigma0, amp, dist, _ptr(s))
     return s
