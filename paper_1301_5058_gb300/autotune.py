@@ -24,7 +24,7 @@ L2_BYTES = 126 * 2 ** 20   # GB300 L2 (about 126 MiB usable)
 # one launch per pass over every instance at either depth; L2-sized groups
 # stepped by resident launches (one stage per pass) are searched only when
 # asked for (RESIDENT_CANDIDATES: they have never won on GB300)
-BATCH_CANDIDATES = [(rows, graph, 0, 0, depth) for depth in (1, 2) for rows in (16, 32, 64)
+BATCH_CANDIDATES = [(rows, graph, 0, 0, depth) for depth in (1, 2) for rows in (16, 32, 64, 128)
                     for graph in (0, 64)]
 RESIDENT_CANDIDATES = [(rows, 0, group, res, 1) for rows in (4, 8, 16)
                        for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)]
