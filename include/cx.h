@@ -156,6 +156,22 @@ int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit);
  * limit), OOM, CUDA.  On error *out is left NULL. */
 int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out);
 
+/* As cx_create, over device arrays the caller owns (e.g. tensors of a
+ * framework whose allocator owns the device memory): b[0], b[1] and n[0],
+ * n[1] (the ping-pong state) and sigma, each ny rows of `pitch` elements of
+ * the state precision (FP32 or FP64 per p->precision) on the current device.
+ * The handle initialises them as cx_create does (sigma field, inoculum; the
+ * second state buffers zeroed) and never frees them: they must outlive the
+ * handle.  Which of b[0] / b[1] holds the current state changes with every
+ * pass; read it through cx_get_field.  Requirements: every pointer non-NULL
+ * and 16-byte aligned, pitch >= nx with pitch x element size a multiple of
+ * 16 bytes (a multiple of 128 bytes is fastest), and no two arrays
+ * overlapping.  Errors: INVALID_ARG (checked before any device work),
+ * DT_UNSTABLE, CUDA.  There is no counterpart in the paper (a memory-ownership
+ * interface). */
+int cx_create_with_buffers(const cx_grid *g, const cx_params *p, uint64_t seed, void *const b[2],
+                           void *const n[2], void *sigma, int64_t pitch, cx_ctx **out);
+
 /* Run all later work of `c` on `stream` (a cudaStream_t, e.g. a torch
  * stream handle; NULL = the legacy default stream). */
 int cx_set_stream(cx_ctx *c, void *stream);

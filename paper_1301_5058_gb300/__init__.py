@@ -78,6 +78,10 @@ _SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_double)]),
     "cx_create": (ctypes.c_int, [ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
                                  ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "cx_create_with_buffers": (ctypes.c_int, [ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
+                                               ctypes.c_uint64, ctypes.POINTER(_P),
+                                               ctypes.POINTER(_P), _P, ctypes.c_int64,
+                                               ctypes.POINTER(_P)]),
     "cx_set_stream": (ctypes.c_int, [_P, _P]),
     "cx_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "cx_synchronize": (ctypes.c_int, [_P]),
@@ -195,6 +199,18 @@ def cx_dt_limit(grid: cx_grid, params: cx_params) -> float:
 def cx_create(grid: cx_grid, params: cx_params, seed: int) -> int:
     h = _P()
     _check(lib().cx_create(ctypes.byref(grid), ctypes.byref(params), seed, ctypes.byref(h)))
+    return h.value
+
+
+def cx_create_with_buffers(grid: cx_grid, params: cx_params, seed: int, b, n, sigma,
+                           pitch: int) -> int:
+    """b, n: two device addresses each (the ping-pong state); sigma: one;
+    every array ny rows of `pitch` elements, owned by the caller."""
+    bb = (_P * 2)(*[int(x) for x in b])
+    nn = (_P * 2)(*[int(x) for x in n])
+    h = _P()
+    _check(lib().cx_create_with_buffers(ctypes.byref(grid), ctypes.byref(params), seed, bb, nn,
+                                        _P(int(sigma)), pitch, ctypes.byref(h)))
     return h.value
 
 

@@ -117,11 +117,11 @@ cx::Coef coef_of(const cx_ctx *c) { return cx::make_coef(c->g, c->p, c->dt); }
 void free_buffers(cx_ctx *c)
 {
     for (int q = 0; q < 2; ++q) {
-        if (c->b[q]) cudaFree(c->b[q]);
-        if (c->n[q]) cudaFree(c->n[q]);
+        if (c->own_fields && c->b[q]) cudaFree(c->b[q]);
+        if (c->own_fields && c->n[q]) cudaFree(c->n[q]);
         c->b[q] = c->n[q] = nullptr;
     }
-    if (c->sigma) cudaFree(c->sigma);
+    if (c->own_fields && c->sigma) cudaFree(c->sigma);
     if (c->diag.partials) cudaFree(c->diag.partials);
     if (c->diag.result) cudaFree(c->diag.result);
     if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -130,8 +130,16 @@ void free_buffers(cx_ctx *c)
     c->h_diag = nullptr;
 }
 
-// Allocate the handle and its buffers (contents: zero).
-int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx_ctx **out)
+// Device arrays a caller provides for the fields (cx_create_with_buffers).
+struct FieldBuffers {
+    void *b[2], *n[2], *sigma;
+    long long pitch;  // elements per row
+};
+
+// Allocate the handle and its buffers, or adopt the caller's field arrays
+// (contents: zero).
+int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx_ctx **out,
+              const FieldBuffers *ext = nullptr)
 {
     cx_ctx *c = new (std::nothrow) cx_ctx;
     if (!c) return fail(CX_ERR_OOM, "host allocation of the handle failed");
@@ -142,7 +150,8 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     c->prec = p->precision;
     c->elem = c->prec == CX_PREC_F64 ? sizeof(double) : sizeof(float);
     const long long align = 128 / (long long)c->elem;  // rows start on 128-byte lines
-    c->pitch = ((long long)g->nx + align - 1) / align * align;
+    c->pitch = ext ? ext->pitch : ((long long)g->nx + align - 1) / align * align;
+    c->own_fields = ext ? 0 : 1;
     c->dt = dt;
     c->tile_rows = 0;  // automatic (auto_tile_rows)
     // two stages per pass pay off for an FP32 state, whose pass is bound by
@@ -153,11 +162,19 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     cudaGetDevice(&c->device);
     const size_t bytes = (size_t)c->pitch * (size_t)g->ny * c->elem;
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
-        e = cudaMalloc(&c->b[q], bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&c->n[q], bytes);
+    if (ext) {
+        for (int q = 0; q < 2; ++q) {
+            c->b[q] = ext->b[q];
+            c->n[q] = ext->n[q];
+        }
+        c->sigma = ext->sigma;
+    } else {
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            e = cudaMalloc(&c->b[q], bytes);
+            if (e == cudaSuccess) e = cudaMalloc(&c->n[q], bytes);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&c->sigma, bytes);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&c->sigma, bytes);
     c->diag.blocks = cx::diag_blocks_for(g->ny);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->diag.partials, 8 * sizeof(double) * c->diag.blocks);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->diag.result, 8 * sizeof(double));
@@ -300,7 +317,8 @@ static int auto_tile_rows(const cx_ctx *c)
 
 static int tile_rows_of(const cx_ctx *c) { return c->tile_rows > 0 ? c->tile_rows : auto_tile_rows(c); }
 
-int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
+static int create_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out,
+                      const FieldBuffers *ext)
 {
     if (!out) return fail(CX_ERR_INVALID_ARG, "out must not be NULL");
     *out = nullptr;
@@ -310,7 +328,7 @@ int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
     rc = resolve_dt(g, p, &dt);
     if (rc) return rc;
     cx_ctx *c;
-    rc = alloc_ctx(g, p, seed, dt, &c);
+    rc = alloc_ctx(g, p, seed, dt, &c, ext);
     if (rc) return rc;
     cudaError_t e = fill_sigma(c, 0);
     if (e == cudaSuccess)
@@ -323,6 +341,37 @@ int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
     }
     *out = c;
     return CX_OK;
+}
+
+int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
+{
+    return create_ctx(g, p, seed, out, nullptr);
+}
+
+int cx_create_with_buffers(const cx_grid *g, const cx_params *p, uint64_t seed, void *const b[2],
+                           void *const n[2], void *sigma, int64_t pitch, cx_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!b || !n) return fail(CX_ERR_INVALID_ARG, "b and n must point to two buffers each");
+    int rc = validate(g, p);
+    if (rc) return rc;
+    FieldBuffers fb{{b[0], b[1]}, {n[0], n[1]}, sigma, (long long)pitch};
+    const size_t elem = p->precision == CX_PREC_F64 ? sizeof(double) : sizeof(float);
+    if (pitch < (int64_t)g->nx || ((size_t)pitch * elem) % 16 != 0)
+        return fail(CX_ERR_INVALID_ARG, "pitch %lld: needs pitch >= nx = %d and rows of a multiple "
+                    "of 16 bytes", (long long)pitch, g->nx);
+    void *ptrs[5] = {fb.b[0], fb.b[1], fb.n[0], fb.n[1], fb.sigma};
+    const unsigned long long span = (unsigned long long)pitch * (unsigned long long)g->ny * elem;
+    for (int i = 0; i < 5; ++i) {
+        if (!ptrs[i] || ((uintptr_t)ptrs[i] & 15) != 0)
+            return fail(CX_ERR_INVALID_ARG, "field buffer %d is NULL or not 16-byte aligned", i);
+        for (int j = 0; j < i; ++j) {
+            const unsigned long long a = (uintptr_t)ptrs[i], q = (uintptr_t)ptrs[j];
+            if (a < q + span && q < a + span)
+                return fail(CX_ERR_INVALID_ARG, "field buffers %d and %d overlap", j, i);
+        }
+    }
+    return create_ctx(g, p, seed, out, &fb);
 }
 
 int cx_set_stream(cx_ctx *c, void *stream)

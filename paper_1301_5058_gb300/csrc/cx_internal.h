@@ -135,6 +135,7 @@ struct cx_ctx {
     long long pitch;      // elements per row (rows 128-byte aligned)
     void *b[2], *n[2];    // ping-pong state
     void *sigma;
+    int own_fields;       // 1: b, n, sigma allocated (and freed) by the library
     int cur;              // index of the buffer holding the current state
     int64_t step;
     double dt;

@@ -121,6 +121,15 @@ def test_create_rejects_unstable_dt(cx):
     assert "stability limit" in cx.cx_last_error()
 
 
+def test_create_with_buffers_checks_pointers_before_device_work(cx):
+    g = cx.cx_grid(64, 16, 1.0)
+    p = cx.cx_params_default(sigma0=4.0)
+    for b, n, s in (([0, 0], [0, 0], 0), ([16, 32], [48, 64], 0), ([17, 4096], [8192, 12288], 16384)):
+        with pytest.raises(cx.CxError) as e:
+            cx.cx_create_with_buffers(g, p, 0, b, n, s, 64)
+        assert e.value.code == cx.CX_ERR_INVALID_ARG
+
+
 def test_null_handles_are_rejected(cx):
     for f, args in ((cx.lib().cx_step, (None, 1)), (cx.lib().cx_synchronize, (None,)),
                     (cx.lib().cx_set_tile_rows, (None, 2)), (cx.lib().cx_set_step, (None, 0)),

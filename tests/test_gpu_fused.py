@@ -152,3 +152,52 @@ def test_autotuner_picks_depth_and_height(cx, tmp_path, monkeypatch):
         assert (cx.cx_get_time_block(sim.h), cx.cx_get_tile_rows(sim.h)) == choice
         again, _ = autotune.tune_single(sim, use_cache=True)
         assert again == choice
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_create_with_caller_buffers(cx, prec):
+    # the fields in device arrays a framework owns (torch tensors here): the
+    # run equals a library-allocated one bit for bit, and the arrays hold it
+    import torch
+    nx, ny, pitch = 300, 77, 320
+    cfg = dict(W.CONFIG0, nx=nx, ny=ny, chi0=1.0, seed=4)
+    grid, params, seed = W.split(cfg)
+    params["precision"] = prec
+    dtype = torch.float64 if prec == 0 else torch.float32
+    b = torch.full((2, ny, pitch), 7.0, dtype=dtype, device="cuda")
+    n = torch.full((2, ny, pitch), 7.0, dtype=dtype, device="cuda")
+    s = torch.full((ny, pitch), 7.0, dtype=dtype, device="cuda")
+    g, p = cx.cx_grid(nx, ny, 1.0), cx.cx_params_default(**params)
+    h = cx.cx_create_with_buffers(g, p, seed, [b[0].data_ptr(), b[1].data_ptr()],
+                                  [n[0].data_ptr(), n[1].data_ptr()], s.data_ptr(), pitch)
+    npd = np.float64 if prec == 0 else np.float32
+    with cx.Sim(nx, ny, 1.0, seed=seed, handle=h, **params) as own, \
+            cx.Sim(nx, ny, 1.0, seed=seed, **params) as ref:
+        torch.cuda.synchronize()
+        assert np.array_equal(s[:, :nx].cpu().numpy(), ref.field(cx.CX_FIELD_SIGMA, npd))
+        for sim in (own, ref):
+            sim.step(37)
+        for w in (cx.CX_FIELD_B, cx.CX_FIELD_N):
+            assert np.array_equal(own.field(w, npd), ref.field(w, npd))
+        cur = own.field(cx.CX_FIELD_B, npd)
+        held = [b[q, :, :nx].cpu().numpy() for q in (0, 1)]
+        assert any(np.array_equal(cur, x) for x in held)
+
+
+def test_create_with_caller_buffers_rejects_bad_layouts(cx):
+    import torch
+    nx, ny, pitch = 64, 16, 64
+    params = dict(W.split(dict(W.CONFIG0, nx=nx, ny=ny))[1], precision=1)
+    g, p = cx.cx_grid(nx, ny, 1.0), cx.cx_params_default(**params)
+    t = torch.zeros((6, ny, pitch), dtype=torch.float32, device="cuda")
+    ptr = [t[i].data_ptr() for i in range(6)]
+    bad = [
+        ([ptr[0], ptr[1]], [ptr[2], ptr[3]], ptr[4], nx - 4),        # pitch < nx
+        ([ptr[0], ptr[1]], [ptr[2], ptr[3]], ptr[4], 66),            # row not 16-byte sized
+        ([ptr[0] + 4, ptr[1]], [ptr[2], ptr[3]], ptr[4], pitch),     # misaligned
+        ([ptr[0], ptr[0] + 256], [ptr[2], ptr[3]], ptr[4], pitch),   # overlapping
+    ]
+    for b, n, s, pt in bad:
+        with pytest.raises(cx.CxError) as e:
+            cx.cx_create_with_buffers(g, p, 0, b, n, s, pt)
+        assert e.value.code == cx.CX_ERR_INVALID_ARG
