@@ -228,6 +228,52 @@ def test_rhs_converges_to_continuous_operator(chemo_law, mobility, order):
 # ---------------------------------------------------------------------------
 # Invariants and symmetries of the full iteration
 
+def _brute_force_step(s, b, n, dx, dt, Dn, theta, chi0):
+    """One forward-Euler step of Eq. ka-chem-model on a tiny grid, cell by
+    cell, each face flux written out from the face means (reading of the
+    discretisation), walls carrying no flux.  Indexing is [y][x]."""
+    ny, nx = b.shape
+    bo, no = np.empty_like(b), np.empty_like(n)
+
+    def flux(P, Q):  # from cell Q into cell P across their shared face
+        sf = 0.5 * (s[P] + s[Q])
+        nf = 0.5 * (n[P] + n[Q])
+        bf = 0.5 * (b[P] + b[Q])
+        chi = chi0 / (1.0 + nf) ** 2
+        Fd = sf * nf * bf * (b[Q] - b[P]) / dx          # Kawasaki cross diffusion
+        Fc = chi * sf * nf * bf * bf * (n[Q] - n[P]) / dx  # nutrient chemotaxis
+        G = Dn * (n[Q] - n[P]) / dx                     # nutrient diffusion
+        return Fd - Fc, G
+
+    for j in range(ny):
+        for i in range(nx):
+            db = dn = 0.0
+            for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+                jj, ii = j + dj, i + di
+                if 0 <= jj < ny and 0 <= ii < nx:
+                    F, G = flux((j, i), (jj, ii))
+                    db += F
+                    dn += G
+            r = n[j, i] * b[j, i]
+            bo[j, i] = b[j, i] + dt * (db / dx + theta * r)
+            no[j, i] = n[j, i] + dt * (dn / dx - r)
+    return bo, no
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 5), (5, 2)])
+def test_one_step_against_brute_force(nx, ny):
+    # tiny non-square grids: every cell touches a wall, so index order (x
+    # fastest), the walls on each side and each face mean are all exercised
+    rng = np.random.default_rng(nx * 10 + ny)
+    s = rng.uniform(1.0, 6.0, (ny, nx))
+    b = rng.uniform(0.05, 0.9, (ny, nx))
+    n = rng.uniform(0.05, 0.9, (ny, nx))
+    kw = dict(dx=0.7, dt=0.013, Dn=1.3, theta=0.8, chi0=1.7)
+    ob, on = oracle.step(s, b, n, **kw)
+    bb, bn = _brute_force_step(s, b, n, **kw)
+    assert np.allclose(ob, bb, rtol=1e-14, atol=0) and np.allclose(on, bn, rtol=1e-14, atol=0)
+
+
 @pytest.mark.parametrize("theta,Dn", [(1.0, 1.0), (0.7, 1.3)])
 def test_conservation_of_b_plus_theta_n(theta, Dn):
     # d/dt int (b + theta n) = 0 for Eq. ka-model-dim with no-flux walls; the
