@@ -51,14 +51,15 @@ def launches_per_window(scheme, time_block, S):
 
 
 # Algorithmic floating-point work per cell-update of the scheme as written
-# (receptor law, central mobility; a multiply-add counts two): 16 flops per
+# (receptor law, central mobility; a multiply-add counts two): 14 flops per
 # face (sums, differences, the receptor weight with one division, the flux
-# products), two faces per cell, 13 for the update; Heun takes two stages and
-# the mean (u0 + u) / 2 of b and n.  Peak rates from the unit counts at the
+# products), two faces per cell, 15 for the update (reaction, divergences and
+# their scale factors); Heun takes two stages and the mean (u0 + u) / 2 of b
+# and n.  Peak rates from the unit counts at the
 # sampled maximum SM clock: 128 FP32 lanes per SM, and for FP64 2
 # multiply-adds per SM and clock (GB300's nominal 1.25 TFLOP/s at 2.07 GHz on
 # 152 SMs), a multiply-add being two flops.
-FLOPS_PER_CELL_UPDATE = {"euler": 2 * 16 + 13, "heun": 2 * (2 * 16 + 13) + 4}
+FLOPS_PER_CELL_UPDATE = {"euler": 2 * 14 + 15, "heun": 2 * (2 * 14 + 15) + 4}
 SMS = 152
 
 
@@ -121,10 +122,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(prec, name):
+def kernel_traffic(prec, name, nx, ny):
     """ncu DRAM bytes per launch of kernel `name` ("step_kernel" or
-    "fused_kernel") on the 16384^2 workload, if recorded for the current
-    sources of that kernel (null otherwise)."""
+    "fused_kernel") on an nx x ny grid, if recorded for that grid and the
+    current sources of that kernel (null otherwise)."""
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     csrc = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc")
     if not os.path.exists(path):
@@ -137,7 +138,9 @@ def kernel_traffic(prec, name):
             return None
     if not rec.get("sources_sha256_16"):
         return None
-    return rec.get(prec, {}).get("dram_bytes_per_launch_16384sq")
+    if nx != ny:
+        return None
+    return rec.get(prec, {}).get(f"dram_bytes_per_launch_{nx}sq")
 
 
 class ClockSampler:
@@ -385,7 +388,7 @@ def main():
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
            "kernel": kernel,
-           "traffic": kernel_traffic(args.precision, kernel),
+           "traffic": kernel_traffic(args.precision, kernel, cfg["nx"], cfg["ny"]),
            "algorithmic_bytes_per_cell": bpc,
            "kernel_ms_per_time_step": per_launch * 1e3,
            # the HBM-roofline rate of a one-step-per-pass stepper
@@ -402,8 +405,9 @@ def main():
         roofline = dict(hbm, alu_fp32=alu)
         if args.time_block == 2:
             roofline["limiter"] = ("instruction issue: two stages per pass halve the HBM bytes "
-                                   "per cell-update, and the pass then issues about 64 thread "
-                                   "instructions per cell-update (ncu)")
+                                   "per cell-update, and the pass then issues about 58 thread "
+                                   "instructions per cell-update (ncu: issue slots 69 % busy, "
+                                   "1.5 eligible warps per cycle at 4 warps per scheduler)")
     out = {
         "metric": "grid-cell updates/s",
         "value": value,

@@ -61,12 +61,12 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         }
         return split4(v);
     };
-    // x-faces of a row; b and n neighbours from the adjacent lanes, sigma's
-    // given (ls, rs); the end lanes take their own values for the one they lack
-    auto xfaces = [&](const Cells<T> &s, const Cells<T> &n, const Cells<T> &b, T ls, T rs) {
+    // x-faces of a row; b and n of cell x0-1 from the left lane, sigma's
+    // given (ls); the face beyond x0+3 is the right lane's first.  The end
+    // lanes take their own values for the neighbour they lack
+    auto xfaces = [&](const Cells<T> &s, const Cells<T> &n, const Cells<T> &b, T ls) {
         const T lb = __shfl_up_sync(kFull, b.O.y, 1), ln = __shfl_up_sync(kFull, n.O.y, 1);
-        const T rb = __shfl_down_sync(kFull, b.E.x, 1), rn = __shfl_down_sync(kFull, n.E.x, 1);
-        return row_xfaces<T, LAW, MOB, INTERIOR>(s, n, b, ls, ln, lb, rs, rn, rb, k, x0, nx);
+        return row_xfaces_shfl<T, LAW, MOB, INTERIOR>(s, n, b, ls, ln, lb, k, x0, nx);
     };
     // y-faces between row (s, n, b)_1 and row (s, n, b)_2 in march order
     auto yfaces = [&](const Cells<T> &s1, const Cells<T> &n1, const Cells<T> &b1,
@@ -81,13 +81,15 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
     YFaces<T> yB0 = zero_yfaces<T>();  // first-stage faces between q - DIR and q
     Cells<T> b1 = zero_cells<T>(), n1 = zero_cells<T>();  // first-stage row o
     Cells<T> s1 = zero_cells<T>();     // second-stage sigma of row o
-    T ls1 = T(0), rs1 = T(0);          // ... and its x-neighbours
+    T ls1 = T(0);                      // ... and its left neighbour
     Cells<T> ub = zero_cells<T>(), un = zero_cells<T>();  // Heun: state row o
     YFaces<T> yB1 = zero_yfaces<T>();  // second-stage faces between o - DIR and o
     bool in_q = false;  // row q lies inside the grid
     bool in_o = false;  // the first stage of row o was computed (row o inside the grid)
 
     const int rfirst = DIR > 0 ? j0 - 2 : jend + 1;
+    // the last row this tile loads, in march order, clipped to the grid
+    const int plast = DIR > 0 ? min(jend + 1, ny - 1) : max(j0 - 2, 0);
     const int iters = (jend - j0) + 4;
     // One iteration.  In the steady state (STEADY: from the fifth iteration
     // on, in a tile whose rows j0-2 .. jend+1 all lie inside the grid) every
@@ -96,9 +98,11 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         constexpr bool STEADY = decltype(steady)::value;
         const int r = rfirst + DIR * p;
         const bool in_r = STEADY || (r >= 0 && r < ny);  // uniform across the block
+        const long long off = (long long)r * pitch + xv;
+        if (DIR > 0 ? r + kPrefetchRows <= plast : r - kPrefetchRows >= plast)
+            prefetch_row<T, NOISE>(P, off + DIR * kPrefetchRows * pitch);
         Cells<T> br = zero_cells<T>(), nr = zero_cells<T>(), sr = zero_cells<T>();
         if (in_r) {
-            const long long off = (long long)r * pitch + xv;
             br = vload(P.b + off);
             nr = vload(P.n + off);
             sr = NOISE == 0 ? vload(P.s + off) : gen_sigma(nz1, r);
@@ -110,11 +114,10 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         const YFaces<T> yA0 = both ? yfaces(s0, n0, b0, sr, nr, br) : zero_yfaces<T>();
         const bool do1 = STEADY || (in_q && p >= 2);
         Cells<T> b1q = zero_cells<T>(), n1q = zero_cells<T>();
-        T ls0 = T(0), rs0 = T(0);
+        T ls0 = T(0);
         if (do1) {
             ls0 = __shfl_up_sync(kFull, s0.O.y, 1);
-            rs0 = __shfl_down_sync(kFull, s0.E.x, 1);
-            const XFaces<T> xf = xfaces(s0, n0, b0, ls0, rs0);
+            const XFaces<T> xf = xfaces(s0, n0, b0, ls0);
             row_update<T, DIR>(b0, n0, xf, yB0, yA0, k, b1q, n1q);
         }
 
@@ -127,11 +130,8 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         const YFaces<T> yA1 = have_o ? yfaces(s1, n1, b1, s2q, n1q, b1q) : zero_yfaces<T>();
         if (STEADY || p >= 4) {
             const int o = r - 2 * DIR;
-            if (!kSameSigma) {
-                ls1 = __shfl_up_sync(kFull, s1.O.y, 1);
-                rs1 = __shfl_down_sync(kFull, s1.E.x, 1);
-            }
-            const XFaces<T> xf = xfaces(s1, n1, b1, ls1, rs1);
+            if (!kSameSigma) ls1 = __shfl_up_sync(kFull, s1.O.y, 1);
+            const XFaces<T> xf = xfaces(s1, n1, b1, ls1);
             Cells<T> ob, on;
             row_update<T, DIR>(b1, n1, xf, yB1, yA1, k, ob, on);
             if (HEUN) {
@@ -170,10 +170,7 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         n0 = nr;
         s0 = sr;
         yB0 = yA0;
-        if (kSameSigma) {
-            ls1 = ls0;
-            rs1 = rs0;
-        }
+        if (kSameSigma) ls1 = ls0;
         in_o = do1;
         in_q = in_r;
     };
