@@ -200,6 +200,28 @@ int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t cou
  * allowed only with CX_NOISE_STATIC (per-step noise regenerates it). */
 int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size_t count);
 
+/* Staged upload of a new state (b and n), overlapping the copies with the
+ * handle's queued work.  cx_stage_state starts host-to-device copies of the
+ * nx*ny arrays `b_host` and `n_host` (row-major, dtype = the state's own
+ * type, CX_F32 or CX_F64; no conversion) into staging arrays the handle
+ * owns, on a copy stream of its own, and returns without waiting: the copies
+ * are asynchronous when the host arrays are pinned (e.g. cudaMallocHost or a
+ * pinned torch tensor), and the caller must keep the arrays valid and
+ * unchanged until the next cx_commit_state has been followed by a
+ * synchronising call (cx_diagnostics, cx_synchronize, ...).  The first call
+ * allocates the staging arrays (two more state-sized arrays).
+ * cx_commit_state makes the staged arrays the current b and n for all work
+ * queued after it: the handle's stream waits for the staged copies (no host
+ * wait), then the arrays swap roles (a device-to-device copy instead when the
+ * state arrays are the caller's, cx_create_with_buffers).  The step counter
+ * and time are unchanged, as with cx_set_field.  A later cx_stage_state
+ * waits, on the copy stream, until the work queued before the last commit is
+ * done with the arrays it overwrites.  Errors: INVALID_ARG (NULL pointers,
+ * wrong dtype or count, a second stage before the commit, a commit with
+ * nothing staged), OOM/CUDA. */
+int cx_stage_state(cx_ctx *c, const void *b_host, const void *n_host, int32_t dtype, size_t count);
+int cx_commit_state(cx_ctx *c);
+
 /* Copy the handle's grid, parameters (with dt resolved) and seed; any
  * output pointer may be NULL. */
 int cx_get_config(cx_ctx *c, cx_grid *g, cx_params *p, uint64_t *seed);

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "cx_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(cx_diag)]),
     "cx_get_field": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_size_t]),
     "cx_set_field": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_size_t]),
+    "cx_stage_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_size_t]),
+    "cx_commit_state": (ctypes.c_int, [_P]),
     "cx_get_config": (ctypes.c_int, [_P, ctypes.POINTER(cx_grid), ctypes.POINTER(cx_params),
                                      ctypes.POINTER(ctypes.c_uint64)]),
     "cx_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
@@ -255,6 +257,38 @@ def cx_get_field(h, which: int, out: np.ndarray) -> np.ndarray:
 def cx_set_field(h, which: int, src: np.ndarray):
     src = np.ascontiguousarray(src)
     _check(lib().cx_set_field(h, which, src.ctypes.data, _host_view(src), src.size))
+
+
+def _host_buffer(a):
+    """(address, CX_F32/CX_F64, elements) of a C-contiguous host array: a
+    numpy array or a CPU torch tensor (pinned, for copies that overlap queued
+    work)."""
+    if hasattr(a, "data_ptr"):
+        if a.device.type != "cpu" or not a.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors")
+        kind = {4: CX_F32, 8: CX_F64}.get(a.element_size()) if a.is_floating_point() else None
+        if kind is None:
+            raise TypeError("host arrays must be float64 or float32")
+        return a.data_ptr(), kind, a.numel()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return a.ctypes.data, _host_view(a), a.size
+
+
+def cx_stage_state(h, b, n):
+    """Start asynchronous uploads of b and n (host arrays of the state's
+    type) into the handle's staging arrays; cx_commit_state makes them the
+    current state.  Both arrays must stay alive and unchanged until that
+    commit has been followed by a synchronising call."""
+    pb, kb, cb = _host_buffer(b)
+    pn, kn, cn = _host_buffer(n)
+    if kb != kn or cb != cn:
+        raise ValueError("b and n must have the same type and size")
+    _check(lib().cx_stage_state(h, pb, pn, kb, cb))
+
+
+def cx_commit_state(h):
+    _check(lib().cx_commit_state(h))
 
 
 def cx_get_config(h):
@@ -510,6 +544,12 @@ class Sim:
 
     def set_field(self, which, arr):
         cx_set_field(self.h, which, arr)
+
+    def stage_state(self, b, n):
+        cx_stage_state(self.h, b, n)
+
+    def commit_state(self):
+        cx_commit_state(self.h)
 
     @property
     def shape(self):

@@ -122,6 +122,15 @@ void free_buffers(cx_ctx *c)
         c->b[q] = c->n[q] = nullptr;
     }
     if (c->own_fields && c->sigma) cudaFree(c->sigma);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    if (c->stage_b) cudaFree(c->stage_b);
+    if (c->stage_n) cudaFree(c->stage_n);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->staged) cudaEventDestroy(c->staged);
+    if (c->stage_free) cudaEventDestroy(c->stage_free);
+    c->stage_b = c->stage_n = nullptr;
+    c->copy_stream = nullptr;
+    c->staged = c->stage_free = nullptr;
     if (c->diag.partials) cudaFree(c->diag.partials);
     if (c->diag.result) cudaFree(c->diag.result);
     if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -584,6 +593,89 @@ int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size
                       cudaMemcpyHostToDevice, c->stream),
             "field copy to device");
     CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
+    return CX_OK;
+}
+
+int cx_stage_state(cx_ctx *c, const void *b_host, const void *n_host, int32_t dtype, size_t count)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!b_host || !n_host) return fail(CX_ERR_INVALID_ARG, "host pointers must not be NULL");
+    const int state_dtype = c->prec == CX_PREC_F64 ? CX_F64 : CX_F32;
+    if (dtype != state_dtype)
+        return fail(CX_ERR_INVALID_ARG, "staged uploads take the state's own type (dtype %d)", state_dtype);
+    if (count != (size_t)c->g.nx * (size_t)c->g.ny)
+        return fail(CX_ERR_INVALID_ARG, "count %zu != nx*ny = %zu", count,
+                    (size_t)c->g.nx * (size_t)c->g.ny);
+    if (c->stage_pending)
+        return fail(CX_ERR_INVALID_ARG, "an upload is already staged: commit it first");
+    const size_t bytes = (size_t)c->pitch * (size_t)c->g.ny * c->elem;
+    if (!c->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&c->stage_b, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->stage_n, bytes);
+        if (e == cudaSuccess && c->pitch != c->g.nx) {
+            // the padding columns stay zero, as in the state arrays
+            e = cudaMemsetAsync(c->stage_b, 0, bytes, c->copy_stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->stage_n, 0, bytes, c->copy_stream);
+        }
+        if (e != cudaSuccess) {
+            if (c->stage_b) cudaFree(c->stage_b);
+            if (c->stage_n) cudaFree(c->stage_n);
+            if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+            if (c->staged) cudaEventDestroy(c->staged);
+            if (c->stage_free) cudaEventDestroy(c->stage_free);
+            c->stage_b = c->stage_n = nullptr;
+            c->copy_stream = nullptr;
+            c->staged = c->stage_free = nullptr;
+            cudaGetLastError();
+            return cuda_fail(e, "staging buffers");
+        }
+    }
+    // the staging arrays may still be read by work queued before the last commit
+    if (c->stage_free_valid) CX_CUDA(cudaStreamWaitEvent(c->copy_stream, c->stage_free, 0), "stage wait");
+    const size_t row = (size_t)c->g.nx * c->elem;
+    CX_CUDA(copy_rows(c->stage_b, (size_t)c->pitch * c->elem, b_host, row, row, c->g.ny,
+                      cudaMemcpyHostToDevice, c->copy_stream),
+            "staged copy of b");
+    CX_CUDA(copy_rows(c->stage_n, (size_t)c->pitch * c->elem, n_host, row, row, c->g.ny,
+                      cudaMemcpyHostToDevice, c->copy_stream),
+            "staged copy of n");
+    CX_CUDA(cudaEventRecord(c->staged, c->copy_stream), "stage event");
+    c->stage_pending = 1;
+    return CX_OK;
+}
+
+int cx_commit_state(cx_ctx *c)
+{
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->stage_pending) return fail(CX_ERR_INVALID_ARG, "no upload is staged");
+    CX_CUDA(cudaStreamWaitEvent(c->stream, c->staged, 0), "commit wait");
+    if (c->own_fields) {
+        // the staged arrays become the current state; the old current
+        // arrays become the staging arrays once the queued work is done
+        void *t = c->b[c->cur];
+        c->b[c->cur] = c->stage_b;
+        c->stage_b = t;
+        t = c->n[c->cur];
+        c->n[c->cur] = c->stage_n;
+        c->stage_n = t;
+    } else {
+        // caller-owned state arrays keep their addresses: copy on the device
+        const size_t row = (size_t)c->g.nx * c->elem, pitch = (size_t)c->pitch * c->elem;
+        CX_CUDA(copy_rows(c->b[c->cur], pitch, c->stage_b, pitch, row, c->g.ny,
+                          cudaMemcpyDeviceToDevice, c->stream),
+                "commit copy of b");
+        CX_CUDA(copy_rows(c->n[c->cur], pitch, c->stage_n, pitch, row, c->g.ny,
+                          cudaMemcpyDeviceToDevice, c->stream),
+                "commit copy of n");
+    }
+    CX_CUDA(cudaEventRecord(c->stage_free, c->stream), "commit event");
+    c->stage_free_valid = 1;
+    c->stage_pending = 0;
     return CX_OK;
 }
 

@@ -145,4 +145,11 @@ struct cx_ctx {
     int time_block;       // explicit stages per pass over the grid (1 or 2)
     cx::DiagScratch diag;
     double *h_diag;       // pinned [8]
+    // staged uploads (cx_stage_state / cx_commit_state), created on first use
+    void *stage_b, *stage_n;    // device staging arrays, library-owned, same pitch
+    cudaStream_t copy_stream;   // the staged host-to-device copies
+    cudaEvent_t staged;         // recorded after the staged copies
+    cudaEvent_t stage_free;     // recorded once the compute stream is done with the staging arrays
+    int stage_pending;          // a staged upload awaits cx_commit_state
+    int stage_free_valid;       // stage_free has been recorded
 };

@@ -133,7 +133,9 @@ def test_create_with_buffers_checks_pointers_before_device_work(cx):
 def test_null_handles_are_rejected(cx):
     for f, args in ((cx.lib().cx_step, (None, 1)), (cx.lib().cx_synchronize, (None,)),
                     (cx.lib().cx_set_tile_rows, (None, 2)), (cx.lib().cx_set_step, (None, 0)),
-                    (cx.lib().cx_set_time_block, (None, 2)), (cx.lib().cx_get_time_block, (None, None))):
+                    (cx.lib().cx_set_time_block, (None, 2)), (cx.lib().cx_get_time_block, (None, None)),
+                    (cx.lib().cx_stage_state, (None, None, None, cx.CX_F32, 0)),
+                    (cx.lib().cx_commit_state, (None,))):
         assert f(*args) == cx.CX_ERR_INVALID_ARG
     cx.lib().cx_destroy(None)  # no-op
 
