@@ -19,15 +19,16 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
-// Per-run coefficients of the scaled face fluxes.  The kernels work with
-// fluxes pre-multiplied by dt/dx, so that one step reads
-//   b' = b + (phiE - phiW + phiN - phiS) + dt theta n b
-//   n' = n + (gE - gW + gN - gS)         - dt n b
+// Per-run coefficients of the face fluxes.  The kernels evaluate unscaled
+// face fluxes and apply the constant factors once per cell, so that one
+// step reads
+//   b' = b + dt theta n b + cA (phiE - phiW + phiN - phiS)
+//   n' = n - dt n b       + cG (gE - gW + gN - gS)
 // with, on a face between L (left/lower) and R (right/upper),
 //   hc  = chi(n_f) / 2 = cChi / (2+n2)^2 (receptor law) or cChi (constant law)
-//   phi = cA s2 n2 b2 (db - hc b2 dn)                   central mobility b_f^2
-//   phi = cA s2 n2 (b2 db - 4 hc b_d^2 dn)              donor-cell mobility b_d^2
-//   g   = cG dn
+//   phi = s2 n2 b2 (db - hc b2 dn)                   central mobility b_f^2
+//   phi = s2 n2 (b2 db - 4 hc b_d^2 dn)              donor-cell mobility b_d^2
+//   g   = dn
 // where s2 = sL+sR, n2 = nL+nR, b2 = bL+bR, db = bR-bL, dn = nR-nL and b_d
 // is b of the lower-n cell.  Derivation: sigma_f n_f b_f = s2 n2 b2 / 8,
 // b_f^2 = b2^2 / 4 and, for the receptor law, chi(n_f) = 4 chi0 / (2+n2)^2.
