@@ -122,10 +122,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(prec, name, nx, ny):
+def kernel_traffic(prec, name, nx, ny, scheme, noise):
     """ncu DRAM bytes per launch of kernel `name` ("step_kernel" or
-    "fused_kernel") on an nx x ny grid, if recorded for that grid and the
-    current sources of that kernel (null otherwise)."""
+    "fused_kernel") on an nx x ny grid, if recorded for that grid, scheme and
+    noise mode and the current sources of that kernel (null otherwise)."""
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     csrc = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc")
     if not os.path.exists(path):
@@ -138,9 +138,10 @@ def kernel_traffic(prec, name, nx, ny):
             return None
     if not rec.get("sources_sha256_16"):
         return None
-    if nx != ny:
+    entry = rec.get(prec, {})
+    if nx != ny or (entry.get("scheme"), entry.get("noise")) != (scheme, noise):
         return None
-    return rec.get(prec, {}).get(f"dram_bytes_per_launch_{nx}sq")
+    return entry.get(f"dram_bytes_per_launch_{nx}sq")
 
 
 class ClockSampler:
@@ -389,7 +390,8 @@ def main():
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
            "kernel": kernel,
-           "traffic": kernel_traffic(args.precision, kernel, cfg["nx"], cfg["ny"]),
+           "traffic": kernel_traffic(args.precision, kernel, cfg["nx"], cfg["ny"], args.scheme,
+                                     args.noise),
            "algorithmic_bytes_per_cell": bpc,
            "kernel_ms_per_time_step": per_launch * 1e3,
            # the HBM-roofline rate of a one-step-per-pass stepper
