@@ -1,0 +1,49 @@
+"""Host-side pieces of bench.py that decide what its JSON line claims: the
+algorithmic bytes and flops behind `roofline`, and which ncu traffic record
+(if any) applies to a run."""
+import json
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_per_cell_update():
+    # read b, n, sigma and write b, n once per pass (FP32: 4 B each)
+    assert bench.bytes_per_cell("f32", "euler", "static", 1) == 20
+    assert bench.bytes_per_cell("f32", "euler", "static", 2) == 10     # two steps per pass
+    assert bench.bytes_per_cell("f64", "euler", "static", 1) == 40
+    assert bench.bytes_per_cell("f32", "euler", "per-step", 1) == 16   # sigma regenerated
+    assert bench.bytes_per_cell("f32", "heun", "per-step", 2) == 16    # one Heun step per pass
+
+
+def test_flop_count_of_the_scheme():
+    # 14 per face, two faces per cell, 15 for the update; Heun: two stages and the mean
+    assert bench.FLOPS_PER_CELL_UPDATE == {"euler": 43, "heun": 90}
+
+
+def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
+    # a copy of the repository's records in a scratch root, so that source
+    # edits can be simulated without touching the tree
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    shutil.copytree(os.path.join(ROOT, "paper_1301_5058_gb300", "csrc"),
+                    root / "paper_1301_5058_gb300" / "csrc")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    rec = json.load(open(root / "profiles" / "fused_kernel_traffic.json"))
+    want = rec["f32"]["dram_bytes_per_launch_16384sq"]
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "static") == want
+    # another grid, scheme, noise mode or precision: no record
+    assert bench.kernel_traffic("f32", "fused_kernel", 4096, 4096, "euler", "static") is None
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "heun", "per-step") is None
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "per-step") is None
+    assert bench.kernel_traffic("f64", "fused_kernel", 16384, 16384, "euler", "static") is None
+    # a kernel source that changed since the capture voids the record
+    src = root / "paper_1301_5058_gb300" / "csrc" / "cx_fused.cuh"
+    src.write_text(src.read_text() + "\n// edited\n")
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "static") is None
