@@ -122,26 +122,48 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(prec, name, nx, ny, scheme, noise):
-    """ncu DRAM bytes per launch of kernel `name` ("step_kernel" or
-    "fused_kernel") on an nx x ny grid, if recorded for that grid, scheme and
-    noise mode and the current sources of that kernel (null otherwise)."""
+def _traffic_record(name):
+    """profiles/<name>_traffic.json, or None when it is missing or any kernel
+    source it lists changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     csrc = os.path.join(ROOT, "paper_1301_5058_gb300", "csrc")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    for src, h in rec.get("sources_sha256_16", {}).items():
+    if not rec.get("sources_sha256_16"):
+        return None
+    for src, h in rec["sources_sha256_16"].items():
         p = os.path.join(csrc, src)
         if not os.path.exists(p) or hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] != h:
             return None
-    if not rec.get("sources_sha256_16"):
+    return rec
+
+
+def kernel_traffic(prec, name, nx, ny, scheme, noise):
+    """ncu DRAM bytes per launch of kernel `name` ("step_kernel" or
+    "fused_kernel") on an nx x ny grid, if recorded for that grid, scheme and
+    noise mode and the current sources of that kernel (null otherwise)."""
+    rec = _traffic_record(name)
+    if rec is None:
         return None
     entry = rec.get(prec, {})
     if nx != ny or (entry.get("scheme"), entry.get("noise")) != (scheme, noise):
         return None
     return entry.get(f"dram_bytes_per_launch_{nx}sq")
+
+
+def sweep_traffic(count, tuning):
+    """ncu DRAM bytes per launch of the two-stage batch kernel on the
+    512-instance sweep, if recorded for this tuning and the current sources
+    (null otherwise)."""
+    rec = _traffic_record("batch_fused_kernel")
+    if rec is None or count != 512:
+        return None
+    entry = rec.get("f32", {})
+    if any(tuning.get(k) != v for k, v in entry.get("tuning", {}).items()):
+        return None
+    return entry.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -516,6 +538,8 @@ def main_sweep(args):
     peak, peak_kind = peaks()
     bpc = bytes_per_cell("f32", "euler", "static", depth)
     achieved = bpc * cells / (kernel_s / (K * S)) / 1e9
+    tuning = {"tile_rows": choice[0], "graph_steps": choice[1], "group_bytes": choice[2],
+              "resident_steps": choice[3], "time_block": depth}
     print(json.dumps({
         "metric": "sweep points/hour", "value": batch_pph, "unit": "points/h", "n_gpus": 1,
         "steps": K, "warmup": Wm, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True,
@@ -524,16 +548,14 @@ def main_sweep(args):
                                f"{sorted(set(s['nx'] for s in specs))}, (n0, chi0, sigma0) log grid, "
                                f"static uniform noise a=0.5, forward Euler, {args.point_steps} steps "
                                f"per point", "cells_per_time_step": cells,
-                   "time_steps_per_step": S, "tuning": {"tile_rows": choice[0], "graph_steps": choice[1],
-                                                        "group_bytes": choice[2],
-                                                        "resident_steps": choice[3],
-                                                        "time_block": depth}},
+                   "time_steps_per_step": S, "tuning": tuning},
         "cell_updates_per_s": cells / per_step,
         "single_instance_points_per_hour": single_pph,
         "single_instance_ms_per_time_step": {str(k): v[0] * 1e3 for k, v in single.items()},
         "speedup_vs_single_instance": batch_pph / single_pph,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": sweep_traffic(args.count, tuning),
                      "kernel": "batch_fused_kernel" if depth == 2 else "batch_step_kernel",
                      "algorithmic_bytes_per_cell": bpc},
         "gpu_launches": K * (launches_per_window("euler", depth, S) + 2),

@@ -47,3 +47,17 @@ def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
     src = root / "paper_1301_5058_gb300" / "csrc" / "cx_fused.cuh"
     src.write_text(src.read_text() + "\n// edited\n")
     assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "static") is None
+
+
+def test_sweep_traffic_record_applies_only_to_its_tuning(tmp_path, monkeypatch):
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    shutil.copytree(os.path.join(ROOT, "paper_1301_5058_gb300", "csrc"),
+                    root / "paper_1301_5058_gb300" / "csrc")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    rec = json.load(open(root / "profiles" / "batch_fused_kernel_traffic.json"))["f32"]
+    tuning = dict(rec["tuning"], graph_steps=64)
+    assert bench.sweep_traffic(512, tuning) == rec["dram_bytes_per_launch"]
+    assert bench.sweep_traffic(256, tuning) is None                       # another sweep
+    assert bench.sweep_traffic(512, dict(tuning, tile_rows=128)) is None   # other tiles
+    assert bench.sweep_traffic(512, dict(tuning, time_block=1)) is None    # one stage per pass
