@@ -19,7 +19,6 @@ n0 in {0.35, 0.71, 1.07, 2, 3, 4} x chi0 in {0, 1, 2.5, 5, 10}.
 from __future__ import annotations
 
 import json
-import math
 import sys
 
 import numpy as np

@@ -2,7 +2,6 @@
 loads, exports every function that include/*.h declares, and rejects bad
 arguments before touching the device."""
 import glob
-import math
 import os
 import re
 

@@ -1,5 +1,4 @@
 """Pins of the oracle's surrogate MLP and morphology labels."""
-import math
 
 import numpy as np
 import pytest
