@@ -228,10 +228,13 @@ def test_rhs_converges_to_continuous_operator(chemo_law, mobility, order):
 # ---------------------------------------------------------------------------
 # Invariants and symmetries of the full iteration
 
-def _brute_force_step(s, b, n, dx, dt, Dn, theta, chi0):
+def _brute_force_step(s, b, n, dx, dt, Dn, theta, chi0, mobility=0):
     """One forward-Euler step of Eq. ka-chem-model on a tiny grid, cell by
     cell, each face flux written out from the face means (reading of the
-    discretisation), walls carrying no flux.  Indexing is [y][x]."""
+    discretisation), walls carrying no flux.  Indexing is [y][x].  With
+    mobility 1 the b^2 of the chemotactic flux is the donor cell's: the cell
+    of the pair with the lower nutrient, the one bacteria leave when they
+    climb the nutrient gradient."""
     ny, nx = b.shape
     bo, no = np.empty_like(b), np.empty_like(n)
 
@@ -240,8 +243,13 @@ def _brute_force_step(s, b, n, dx, dt, Dn, theta, chi0):
         nf = 0.5 * (n[P] + n[Q])
         bf = 0.5 * (b[P] + b[Q])
         chi = chi0 / (1.0 + nf) ** 2
+        if mobility == 0:
+            m = bf * bf
+        else:
+            donor = P if n[P] < n[Q] else Q     # equal n: no chemotactic flux either way
+            m = b[donor] ** 2
         Fd = sf * nf * bf * (b[Q] - b[P]) / dx          # Kawasaki cross diffusion
-        Fc = chi * sf * nf * bf * bf * (n[Q] - n[P]) / dx  # nutrient chemotaxis
+        Fc = chi * sf * nf * m * (n[Q] - n[P]) / dx     # nutrient chemotaxis
         G = Dn * (n[Q] - n[P]) / dx                     # nutrient diffusion
         return Fd - Fc, G
 
@@ -260,18 +268,69 @@ def _brute_force_step(s, b, n, dx, dt, Dn, theta, chi0):
     return bo, no
 
 
+@pytest.mark.parametrize("mobility", [0, 1])
 @pytest.mark.parametrize("nx,ny", [(3, 3), (4, 5), (5, 2)])
-def test_one_step_against_brute_force(nx, ny):
+def test_one_step_against_brute_force(nx, ny, mobility):
     # tiny non-square grids: every cell touches a wall, so index order (x
-    # fastest), the walls on each side and each face mean are all exercised
+    # fastest), the walls on each side and each face mean are all exercised;
+    # random n makes the donor fall on either side of the faces
     rng = np.random.default_rng(nx * 10 + ny)
     s = rng.uniform(1.0, 6.0, (ny, nx))
     b = rng.uniform(0.05, 0.9, (ny, nx))
     n = rng.uniform(0.05, 0.9, (ny, nx))
     kw = dict(dx=0.7, dt=0.013, Dn=1.3, theta=0.8, chi0=1.7)
-    ob, on = oracle.step(s, b, n, **kw)
-    bb, bn = _brute_force_step(s, b, n, **kw)
+    ob, on = oracle.step(s, b, n, mobility=mobility, **kw)
+    bb, bn = _brute_force_step(s, b, n, mobility=mobility, **kw)
     assert np.allclose(ob, bb, rtol=1e-14, atol=0) and np.allclose(on, bn, rtol=1e-14, atol=0)
+    # the two mobilities really differ on these fields, so each is pinned apart
+    cb, _ = _brute_force_step(s, b, n, mobility=1 - mobility, **kw)
+    assert np.max(np.abs(cb - bb)) > 1e-6
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("empty_side", [0, 1])
+@pytest.mark.parametrize("law", [0, 1])
+def test_donor_cell_keeps_an_empty_lower_nutrient_cell_nonnegative(axis, empty_side, law):
+    # Two cells, one empty of bacteria.  Chemotaxis carries bacteria up the
+    # nutrient gradient (Eq. chemflux), so across the face it moves them out
+    # of the lower-n cell into the higher-n one.  Reading c3: the donor-cell
+    # mobility takes b^2 of the lower-n cell.
+    #   (a) empty cell has the LOWER n: it is the donor and holds nothing, so
+    #       no chemotactic flux crosses the face at any chi0 -- its update is
+    #       the chi0 = 0 update bit for bit and it stays >= 0, while the central
+    #       b_f^2 drives it negative once chi0 is large;
+    #   (b) empty cell has the HIGHER n: the full cell is the donor, so the
+    #       chemotactic flux is chi(n_f) s_f n_f b_full^2 dn / dx, computed here
+    #       by hand.  A donor taken from the wrong side would give 0 in (b) and
+    #       a negative cell in (a).
+    dx, dt, theta, Dn = 0.5, 1e-3, 1.0, 1.0
+    s0 = np.array([2.0, 3.0])
+    bfull, nlo, nhi = 0.6, 0.2, 0.9
+    for empty_is_low in (True, False):
+        b = np.array([0.0, bfull]) if empty_side == 0 else np.array([bfull, 0.0])
+        ne = nlo if empty_is_low else nhi
+        nf_ = nhi if empty_is_low else nlo
+        n = np.array([ne, nf_]) if empty_side == 0 else np.array([nf_, ne])
+        shape = (1, 2) if axis == 0 else (2, 1)
+        S, B, N = (a.reshape(shape) for a in (s0, b, n))
+        e = empty_side
+        chi0 = 200.0
+        kw = dict(dx=dx, Dn=Dn, theta=theta, chemo_law=law)
+        rb, _ = oracle.rhs(S, B, N, chi0=chi0, mobility=1, **kw)
+        rb0, _ = oracle.rhs(S, B, N, chi0=0.0, mobility=1, **kw)
+        rbc, _ = oracle.rhs(S, B, N, chi0=chi0, mobility=0, **kw)
+        rb, rb0, rbc = rb.ravel(), rb0.ravel(), rbc.ravel()
+        if empty_is_low:
+            assert rb[e] == rb0[e] and rb[e] > 0.0
+            assert rbc[e] < 0.0                   # central mobility: negative after one step
+            bb, _ = oracle.step(S, B, N, dt=dt, chi0=chi0, mobility=1, **kw)
+            assert bb.ravel()[e] >= 0.0
+        else:
+            sf, nfc = 0.5 * (s0[0] + s0[1]), 0.5 * (nlo + nhi)
+            chi = chi0 / (1 + nfc) ** 2 if law == 0 else chi0
+            Fc = chi * sf * nfc * bfull ** 2 * (nhi - nlo) / dx
+            # the chemotactic part of the empty cell's rate: Fc / dx into it
+            assert rb[e] - rb0[e] == pytest.approx(Fc / dx, rel=1e-13)
 
 
 @pytest.mark.parametrize("theta,Dn", [(1.0, 1.0), (0.7, 1.3)])
@@ -350,6 +409,36 @@ def test_per_step_noise_uses_step_index():
         s = oracle.sigma_field(nx, ny, 9, 4.0, 1.0, dist=1, step=m)
         b1, n1 = oracle.step(s, b1, n1, dx=1.0, dt=0.005, Dn=1.0, theta=1.0, chi0=0.5)
     assert np.array_equal(bb, b1) and np.array_equal(nn, n1)
+
+
+# ---------------------------------------------------------------------------
+# Stability limit (reading c7), both branches by hand
+
+def test_dt_limit_diffusive_branch_by_hand():
+    # config 0: B = bM + theta n0 = 1.2, sigma_max = 4 (1 + 0.5) = 6,
+    # D = 6 * 0.7 * 1.2 * (1 + 0.5 * 1.2) = 8.064 > Dn, so the limit is
+    # dx^2 / (4 D) = 1 / 32.256 (the reaction branch is 1 / 5.2)
+    lim = oracle.dt_limit(dx=1.0, Dn=1.0, theta=1.0, chi0=0.5, n0=0.7, bM=0.5, sigma0=4.0, amp=0.5)
+    assert lim == pytest.approx(1.0 / 32.256, rel=1e-15)
+
+
+def test_dt_limit_reaction_branch_by_hand():
+    # Dn = 10 dominates the cross diffusion (sigma_max n0 B (1 + chi0 B) =
+    # 0.5 * 0.5 * 1.0 * 1 = 0.25), so Dmax = Dn and the diffusive branch is
+    # dx^2 / (4 Dn) = 0.25 / 40 = 1/160; the branch that keeps n >= 0 under
+    # Euler, 1 / (4 Dn / dx^2 + B) = 1 / (160 + 1), is smaller and decides
+    lim = oracle.dt_limit(dx=0.5, Dn=10.0, theta=1.0, chi0=0.0, n0=0.5, bM=0.5, sigma0=0.5, amp=0.0)
+    assert lim == pytest.approx(1.0 / 161.0, rel=1e-15)
+    # and that branch is what it says: with b = B everywhere (the largest b the
+    # reading allows) and an n checkerboard, one Euler step at the limit takes
+    # the low cells to exactly 0 and no lower
+    nx = ny = 6
+    n = np.where((np.add.outer(np.arange(ny), np.arange(nx)) % 2) == 0, 1.0, 0.0)
+    b = np.full((ny, nx), 1.0)
+    s = np.zeros((ny, nx))
+    _, nn = oracle.step(s, b, n, dx=0.5, dt=lim, Dn=10.0, theta=1.0, chi0=0.0)
+    interior = (slice(1, -1), slice(1, -1))
+    assert nn[interior].min() >= -1e-15
 
 
 # ---------------------------------------------------------------------------
