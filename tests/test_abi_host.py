@@ -63,12 +63,16 @@ def test_params_default_is_the_normalised_model(cx):
 
 @pytest.mark.parametrize("chi0,sigma0,amp,n0,bM,dx", [(0.5, 4.0, 0.5, 0.7, 0.5, 1.0),
                                                        (1.0, 4.0, 0.8, 0.35, 0.71, 1.0),
-                                                       (5.0, 1.0, 1.0, 1.07, 0.71, 0.332)])
+                                                       (5.0, 1.0, 1.0, 1.07, 0.71, 0.332),
+                                                       # reaction branch 1/(4 Dn/dx^2 + B) = 1/17 decides
+                                                       (0.0, 0.5, 0.0, 0.5, 0.5, 0.5)])
 def test_dt_limit_matches_oracle(cx, chi0, sigma0, amp, n0, bM, dx):
     p = cx.cx_params_default(chi0=chi0, sigma0=sigma0, noise_amp=amp, n0=n0, bM=bM)
     lim = cx.cx_dt_limit(cx.cx_grid(8, 8, dx), p)
     ref = oracle.dt_limit(dx=dx, Dn=1.0, theta=1.0, chi0=chi0, n0=n0, bM=bM, sigma0=sigma0, amp=amp)
     assert lim == pytest.approx(ref, rel=1e-15)
+    if dx == 0.5:
+        assert lim == pytest.approx(1.0 / 17.0, rel=1e-15)
 
 
 def test_config0_time_step(cx):
