@@ -2,10 +2,20 @@
 workload (n0 = 0.35, sigma0 = 4, a = 0.8, chi0 = 1, inoculum bM = 0.71 with
 r0^2 = 32^2, dt = 0.2 x the stability limit).
 
-One benchmark step = `--window` time steps (one fused kernel launch each)
-followed by one diagnostics reduction (masses, invariant, envelope radius).
-The metric is grid-cell updates per second.  Every input is larger than L2
-(3.2 GB read per time step), so no L2 flush is needed between iterations.
+One benchmark step = `--window` time steps (one fused kernel launch per two
+time steps) followed by one diagnostics reduction (masses, invariant,
+envelope radius).  The metric is grid-cell updates per second.  Every input
+is larger than L2 (3.2 GB read per time step), so no L2 flush is needed
+between iterations.
+
+The same line carries, under "records", the other parts of the metric,
+each timed the same way with its own roofline and clock samples: the FP64
+state at 4096^2 (against the FP64 pipe's rate, measured in this run by
+cx_alu_peak), the paper's own scheme (Heun, sigma redrawn every step from a
+triangular law) at 16384^2, and the 512-instance batched parameter sweep
+(sweep points per hour).  The CPU leg times the FP64 oracle on one core and
+on all host cores, and checks each record's path against the oracle on a
+small case of the same configuration ("oracle_error").
 
 Multi-GPU (torchrun): every rank runs its own replica of the grid (the
 workload partitions into independent simulations; no data-path
@@ -91,26 +101,35 @@ def parse():
     ap.add_argument("--count", type=int, default=512, help="sweep instances")
     ap.add_argument("--point-steps", type=int, default=20000, help="time steps per sweep point")
     ap.add_argument("--tune", action="store_true", help="autotune the batch before timing")
+    ap.add_argument("--no-records", action="store_true",
+                    help="time only the headline grid (no FP64, paper-scheme or sweep records)")
     return ap.parse_args()
 
 
-def workload(args):
+def workload(spec):
+    """The single-grid workload dict of a spec (a dict with n and chi0, or
+    the parsed command line)."""
     from paper_1301_5058_gb300 import workloads as W
-    cfg = dict(W.CONFIG1, nx=args.n, ny=args.n, chi0=args.chi0)
-    return cfg
+    get = spec.get if isinstance(spec, dict) else lambda k: getattr(spec, k)
+    return dict(W.CONFIG1, nx=get("n"), ny=get("n"), chi0=get("chi0"))
 
 
-def config_block(args, cfg):
-    return {"workload": f"single grid {cfg['nx']}x{cfg['ny']} {args.precision} state, "
+def config_block(spec, cfg, world=1):
+    get = spec.get if isinstance(spec, dict) else lambda k: getattr(spec, k)
+    w = 4 if get("precision") == "f32" else 8
+    fields = 2 if get("noise") == "per-step" else 3
+    read = fields * cfg["nx"] * cfg["ny"] * w
+    return {"workload": f"single grid {cfg['nx']}x{cfg['ny']} {get('precision')} state, "
                         f"n0={cfg['n0']} sigma0={cfg['sigma0']} a={cfg['noise_amp']} "
-                        f"chi0={cfg['chi0']} receptor law, {args.noise} {args.dist} noise, "
-                        f"{'forward Euler' if args.scheme == 'euler' else 'Heun RK2'}, "
+                        f"chi0={cfg['chi0']} receptor law, {get('noise')} {get('dist')} noise, "
+                        f"{'forward Euler' if get('scheme') == 'euler' else 'Heun RK2'}, "
                         f"dt=0.2 x limit",
-            "nx": cfg["nx"], "ny": cfg["ny"], "time_steps_per_step": args.window,
-            "time_block": args.time_block,
+            "nx": cfg["nx"], "ny": cfg["ny"], "time_steps_per_step": get("window"),
+            "time_block": get("time_block"),
             "diagnostics_per_step": 1,
-            "l2": "inputs larger than L2 (3 fields x 1 GiB read per time step); no flush",
-            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+            "l2": f"inputs larger than L2 ({fields} fields x {read / fields / 2**20:.0f} MiB read "
+                  "per pass); no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def peaks():
@@ -245,32 +264,54 @@ def max_over_ranks(values, world):
     return [float(v) for v in t.tolist()]
 
 
-def run_ours(args, rank, world, local_rank):
+def grid_spec(args):
+    """What one single-grid measurement runs, from the command line."""
+    return dict(n=args.n, chi0=args.chi0, precision=args.precision, scheme=args.scheme,
+                noise=args.noise, dist=args.dist, time_block=args.time_block,
+                window=args.window)
+
+
+def _sim_params(cx, spec, cfg):
+    from paper_1301_5058_gb300 import workloads as W
+    grid, params, seed = W.split(cfg)
+    params["precision"] = cx.CX_PREC_F32 if spec["precision"] == "f32" else cx.CX_PREC_F64
+    params["scheme"] = cx.CX_SCHEME_EULER if spec["scheme"] == "euler" else cx.CX_SCHEME_HEUN
+    params["noise_mode"] = cx.CX_NOISE_STATIC if spec["noise"] == "static" else cx.CX_NOISE_PER_STEP
+    params["noise_dist"] = cx.CX_NOISE_UNIFORM if spec["dist"] == "uniform" else cx.CX_NOISE_TRIANGULAR
+    return grid, params, seed
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        i = dev.index or 0
+        return os.environ.get("CUDA_VISIBLE_DEVICES", str(i)).split(",")[i]
+
+
+def run_grid(spec, K, Wm, rank, world, local_rank, with_e2e):
+    """Time K benchmark steps (after Wm warm-up steps) of one single grid;
+    with_e2e also times the same loop end to end with host buffers."""
     import ctypes
 
-    import numpy as np
     import torch
 
     import paper_1301_5058_gb300 as cx
-    from paper_1301_5058_gb300 import workloads as W
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cfg = workload(args)
-    grid, params, seed = W.split(cfg)
-    params["precision"] = cx.CX_PREC_F32 if args.precision == "f32" else cx.CX_PREC_F64
-    params["scheme"] = cx.CX_SCHEME_EULER if args.scheme == "euler" else cx.CX_SCHEME_HEUN
-    params["noise_mode"] = cx.CX_NOISE_STATIC if args.noise == "static" else cx.CX_NOISE_PER_STEP
-    params["noise_dist"] = cx.CX_NOISE_UNIFORM if args.dist == "uniform" else cx.CX_NOISE_TRIANGULAR
+    cfg = workload(spec)
+    grid, params, seed = _sim_params(cx, spec, cfg)
     seed = replica_seed(seed, rank)
     sim = cx.Sim(grid["nx"], grid["ny"], grid["dx"], seed=seed, **params)
     stream = torch.cuda.current_stream(dev)
     cx.cx_set_stream(sim.h, stream.cuda_stream)
-    if args.time_block is not None:
-        cx.cx_set_time_block(sim.h, args.time_block)
-    args.time_block = cx.cx_get_time_block(sim.h)
+    if spec["time_block"] is not None:
+        cx.cx_set_time_block(sim.h, spec["time_block"])
+    time_block = cx.cx_get_time_block(sim.h)
     cells = cfg["nx"] * cfg["ny"]
-    K, Wm, S = args.steps, args.warmup, args.window
+    S = spec["window"]
 
     def barrier():
         if world > 1:
@@ -292,11 +333,7 @@ def run_ours(args, rank, world, local_rank):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_uuid(dev)) as clk:
         start.record(stream)
         for k in range(K):
             d = bench_step(evs[k])
@@ -305,16 +342,16 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     elapsed = start.elapsed_time(stop) / 1e3
     kernel_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-    per_launch = kernel_s / (K * S)
+    per_step = kernel_s / (K * S)
 
     # end to end through the C ABI with host buffers: every step uploads its
     # inputs (b, n) from pinned host memory and reads the diagnostics back.
     # The upload of the next step's inputs is staged (cx_stage_state) while
     # the current step computes, and committed before that step starts.
     e2e = None
-    if not args.no_e2e:
-        np_dtype = np.float32 if args.precision == "f32" else np.float64
-        hb = torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float32 if np_dtype == np.float32 else torch.float64,
+    if with_e2e:
+        f32 = spec["precision"] == "f32"
+        hb = torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float32 if f32 else torch.float64,
                          pin_memory=True)
         hn = torch.empty_like(hb, pin_memory=True)
         cx.cx_get_field(sim.h, cx.CX_FIELD_B, hb.numpy())
@@ -342,13 +379,83 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": ctypes.sizeof(cx.cx_diag) + 64}
     diag = d.as_dict()
     sim.close()
-    return {"elapsed": elapsed, "kernel_s": kernel_s, "per_launch": per_launch, "cells": cells,
-            "clocks": clk.summary(), "e2e": e2e, "diag": diag, "cfg": cfg}
+    return {"elapsed": elapsed, "kernel_s": kernel_s, "per_step": per_step, "cells": cells,
+            "clocks": clk.summary(), "e2e": e2e, "diag": diag, "cfg": cfg,
+            "time_block": time_block}
 
 
-def cpu_baseline_sample(cfg, side=4096, steps=8):
-    """Time the FP64 oracle (single thread, as it stands) on the central
-    side x side window of the workload for `steps` time steps."""
+LIMITER_TB2 = ("instruction issue: two stages per pass halve the HBM bytes per cell-update, "
+               "and the pass is then held by the thread instructions it issues per cell "
+               "(profiles/fused_kernel_f32_16384sq.md)")
+LIMITER_HEUN = ("instruction issue: both Heun stages and the Philox draw of sigma run in one "
+                "pass, so each cell-update issues two stages' face arithmetic plus the "
+                "generator (profiles/fused_kernel_f32_16384sq.md)")
+
+
+def grid_line(spec, r, K, world, peak, peak_kind, alu_peaks):
+    """The JSON fields of one single-grid measurement."""
+    cfg, cells, S = r["cfg"], r["cells"], spec["window"]
+    tb = r["time_block"]
+    prec, scheme, noise = spec["precision"], spec["scheme"], spec["noise"]
+    units = cells * S * K * world
+    bpc = bytes_per_cell(prec, scheme, noise, tb)
+    lpw = launches_per_window(scheme, tb, S)
+    kernel = "fused_kernel" if tb == 2 else "step_kernel"
+    per_step = r["per_step"]
+    rate = cells / per_step  # cell-updates/s of the step kernels alone
+    sm_mhz = r["clocks"].get("sm_max_mhz") or 2070.0
+    measured = alu_peaks.get(prec)
+    alu = {"bound": "alu", "unit": "TFLOP/s",
+           "flops_per_cell_update": FLOPS_PER_CELL_UPDATE[scheme],
+           "achieved": FLOPS_PER_CELL_UPDATE[scheme] * rate / 1e12}
+    if measured:
+        alu["peak"] = measured / 1e12
+        alu["peak_kind"] = ("measured in this run: cx_alu_peak, register-only multiply-add "
+                            f"kernel in {prec}")
+    else:
+        alu["peak"] = alu_peak_tflops(prec, sm_mhz)
+        alu["peak_kind"] = (f"derived: {'128 FP32' if prec == 'f32' else '2 FP64'} multiply-adds "
+                            f"per SM and clock x {SMS} SMs x {sm_mhz:.0f} MHz")
+    alu["frac"] = alu["achieved"] / alu["peak"]
+    achieved = bpc * rate / 1e9
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+           "kernel": kernel,
+           "traffic": kernel_traffic(prec, kernel, cfg["nx"], cfg["ny"], scheme, noise),
+           "algorithmic_bytes_per_cell": bpc,
+           "kernel_ms_per_time_step": per_step * 1e3,
+           # the HBM-roofline rate of a one-step-per-pass stepper (20 B per
+           # FP32 cell-update): temporal blocking may pass it
+           "one_step_pass_roofline_cell_updates_per_s":
+               peak * 1e9 / bytes_per_cell(prec, scheme, noise, 1),
+           "kernel_cell_updates_per_s": rate,
+           "launches_per_time_step": lpw / S}
+    if prec == "f64":
+        # the FP64 pass is bound by the FP64 pipe: that is its roofline
+        roofline = dict(alu, kernel=kernel, traffic=hbm["traffic"], kernel_cell_updates_per_s=rate,
+                        kernel_ms_per_time_step=per_step * 1e3, hbm=hbm)
+    else:
+        roofline = dict(hbm, alu_fp32=alu)
+        if tb == 2:
+            roofline["limiter"] = LIMITER_TB2 if scheme == "euler" else LIMITER_HEUN
+    return {
+        "value": units / r["elapsed"],
+        "unit": "cell-updates/s",
+        "ms_per_step": r["elapsed"] / K * 1e3,
+        "dtype": prec,
+        "config": config_block(dict(spec, time_block=tb), cfg, world),
+        "roofline": roofline,
+        "gpu_launches": K * (lpw + 2),
+        "clocks": r["clocks"],
+        "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b",
+                                                        "min_n")},
+    }
+
+
+def cpu_baseline_sample(cfg, side=4096, steps=8, threads=0):
+    """Time the FP64 oracle (as it stands; threads > 0: its threaded build
+    on that many host threads) on the central side x side window of the
+    workload for `steps` time steps."""
     import oracle
     # same parameters and noise law; the inoculum sits at the window's centre
     s = oracle.sigma_field(side, side, cfg["seed"], cfg["sigma0"], cfg["noise_amp"])
@@ -356,12 +463,115 @@ def cpu_baseline_sample(cfg, side=4096, steps=8):
     dt = cfg["cfl_frac"] * oracle.dt_limit(dx=cfg["dx"], Dn=cfg["Dn"], theta=cfg["theta"],
                                            chi0=cfg["chi0"], n0=cfg["n0"], bM=cfg["bM"],
                                            sigma0=cfg["sigma0"], amp=cfg["noise_amp"])
+    kw = dict(dx=cfg["dx"], dt=dt, Dn=cfg["Dn"], theta=cfg["theta"], chi0=cfg["chi0"],
+              threads=threads)
+    if threads:
+        oracle.run(s, b, n, 1, **kw)  # build and warm the threaded library
     t0 = time.perf_counter()
-    oracle.run(s, b, n, steps, dx=cfg["dx"], dt=dt, Dn=cfg["Dn"], theta=cfg["theta"],
-               chi0=cfg["chi0"])
+    oracle.run(s, b, n, steps, **kw)
     sec = time.perf_counter() - t0
+    how = "threaded build, gcc -O2 -fopenmp" if threads else "gcc -O2, one thread"
     return side * side * steps / sec, sec, \
-        f"central {side}x{side} window of the workload, {steps} FP64 oracle steps ({sec:.1f} s)"
+        f"central {side}x{side} window of the workload, {steps} FP64 oracle steps ({sec:.1f} s; {how})"
+
+
+# ---------------------------------------------------------------------------
+# The CPU leg's parity checks: each record's path, on a small grid of the same
+# configuration, against the FP64 oracle from the same initial state.
+
+ORACLE_CHECK_STEPS = 200
+
+
+def _rel_l2(x, y):
+    import numpy as np
+    d = float(np.linalg.norm((np.asarray(x, np.float64) - y).ravel()))
+    return d / max(float(np.linalg.norm(np.asarray(y).ravel())), 1e-300)
+
+
+def _oracle_reference(cfg, spec, nx, ny, seed, steps):
+    """The oracle's run of `steps` steps of configuration cfg on nx x ny;
+    returns (b0, n0, b, n)."""
+    import oracle
+    per_step = spec["noise"] == "per-step"
+    dist = 0 if spec["dist"] == "uniform" else 1
+    s = oracle.sigma_field(nx, ny, seed, cfg["sigma0"], cfg["noise_amp"], dist=dist)
+    b0, n0 = oracle.initial_state(nx, ny, cfg["dx"], cfg["n0"], cfg["bM"], cfg["r0sq"])
+    dt = cfg["cfl_frac"] * oracle.dt_limit(dx=cfg["dx"], Dn=cfg["Dn"], theta=cfg["theta"],
+                                           chi0=cfg["chi0"], n0=cfg["n0"], bM=cfg["bM"],
+                                           sigma0=cfg["sigma0"], amp=cfg["noise_amp"])
+    b, n, _ = oracle.run(s, b0, n0, steps, dx=cfg["dx"], dt=dt, Dn=cfg["Dn"], theta=cfg["theta"],
+                         chi0=cfg["chi0"], scheme=0 if spec["scheme"] == "euler" else 1,
+                         noise_mode=1 if per_step else 0, seed=seed, sigma0=cfg["sigma0"],
+                         amp=cfg["noise_amp"], dist=dist,
+                         recipe=1 if spec["precision"] == "f32" else 0)
+    return b0, n0, b, n
+
+
+def oracle_error_grid(spec, nx=288, ny=200, steps=ORACLE_CHECK_STEPS):
+    """Relative L2 error of the record's path (precision, scheme, noise,
+    stages per pass) against the oracle on an nx x ny grid of the same
+    parameters, from the oracle's initial state."""
+    import paper_1301_5058_gb300 as cx
+    cfg = dict(workload(spec), nx=nx, ny=ny)
+    grid, params, seed = _sim_params(cx, spec, cfg)
+    b0, n0, ob, on = _oracle_reference(cfg, spec, nx, ny, seed, steps)
+    with cx.Sim(nx, ny, grid["dx"], seed=seed, **params) as sim:
+        if spec["time_block"] is not None:
+            cx.cx_set_time_block(sim.h, spec["time_block"])
+        sim.set_field(cx.CX_FIELD_B, b0)
+        sim.set_field(cx.CX_FIELD_N, n0)
+        sim.step(steps)
+        gb, gn = sim.field(cx.CX_FIELD_B), sim.field(cx.CX_FIELD_N)
+        tb = cx.cx_get_time_block(sim.h)
+    tol = 1e-4 if spec["precision"] == "f32" else 1e-12
+    eb, en = _rel_l2(gb, ob), _rel_l2(gn, on)
+    return {"rel_l2_b": eb, "rel_l2_n": en, "tolerance": tol, "pass": max(eb, en) <= tol,
+            "case": f"{nx}x{ny}, {steps} steps, same parameters, stages per pass {tb}, "
+                    f"oracle's initial state"}
+
+
+def oracle_error_sweep(tuning, steps=ORACLE_CHECK_STEPS):
+    """The batch path with the sweep's tuning, on three instances of the
+    sweep's kind (smaller sides, one ragged), each against the oracle."""
+    import paper_1301_5058_gb300 as cx
+    from paper_1301_5058_gb300 import workloads as W
+    specs = W.sweep_specs(3, seed=0, steps=steps)
+    for sp, side in zip(specs, (160, 224, 97)):
+        sp["nx"] = sp["ny"] = side
+    spec = dict(precision="f32", scheme="euler", noise="static", dist="uniform")
+    worst = (0.0, 0.0)
+    with cx.Batch(specs) as bt:
+        bt.tune(tuning["tile_rows"], tuning["graph_steps"], tuning["group_bytes"],
+                tuning["resident_steps"], tuning["time_block"])
+        refs = []
+        for i, sp in enumerate(specs):
+            cfg = dict(W.CONFIG1, **{k: v for k, v in sp.items() if k != "precision"})
+            b0, n0, ob, on = _oracle_reference(cfg, spec, sp["nx"], sp["ny"], sp["seed"], steps)
+            bt.set_field(i, cx.CX_FIELD_B, b0)
+            bt.set_field(i, cx.CX_FIELD_N, n0)
+            refs.append((ob, on))
+        bt.step(steps)
+        for i, (ob, on) in enumerate(refs):
+            gb, gn = bt.field(i, cx.CX_FIELD_B), bt.field(i, cx.CX_FIELD_N)
+            worst = (max(worst[0], _rel_l2(gb, ob)), max(worst[1], _rel_l2(gn, on)))
+    return {"rel_l2_b": worst[0], "rel_l2_n": worst[1], "tolerance": 1e-4,
+            "pass": max(worst) <= 1e-4,
+            "case": f"3 instances (160^2, 224^2, 97^2) of the sweep's kind, {steps} steps, "
+                    "the sweep's tuning, worst instance"}
+
+
+def measure_alu_peaks():
+    """FP64 and FP32 multiply-add rates of this GPU, measured by cx_alu_peak."""
+    import paper_1301_5058_gb300 as cx
+    return {"f64": cx.cx_alu_peak(cx.CX_PREC_F64), "f32": cx.cx_alu_peak(cx.CX_PREC_F32)}
+
+
+RECORDS = {
+    "fp64_4096": dict(n=4096, precision="f64", scheme="euler", noise="static", dist="uniform",
+                      time_block=None),
+    "paper_scheme_16384": dict(n=16384, precision="f32", scheme="heun", noise="per-step",
+                               dist="triangular", time_block=None),
+}
 
 
 def main():
@@ -373,84 +583,78 @@ def main():
     if args.impl == "reference":
         return main_reference(args, rank, world)
     if args.workload == "sweep":
-        return main_sweep(args)
+        import torch
+        torch.cuda.set_device(local_rank)
+        rec = sweep_record(args)
+        if not args.no_cpu_baseline:
+            rec["oracle_error"] = oracle_error_sweep(rec["config"]["tuning"])
+        print(json.dumps(dict({"metric": "sweep points/hour", "n_gpus": 1, "steps": args.steps,
+                               "warmup": args.warmup, "higher_is_better": True,
+                               "scaling": "weak", "vs_baseline": None, "data": "synthetic"},
+                              **rec)))
+        return
 
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import torch
+    torch.cuda.set_device(local_rank)
+    alu_peaks = measure_alu_peaks()
 
-    r = run_ours(args, rank, world, local_rank)
+    spec = grid_spec(args)
+    K = args.steps
+    r = run_grid(spec, K, args.warmup, rank, world, local_rank, not args.no_e2e)
+    elapsed, e2e_s, per_step = max_over_ranks(
+        [r["elapsed"], (r["e2e"] or {}).get("seconds") or 0.0, r["per_step"]], world)
+    r.update(elapsed=elapsed, per_step=per_step)
 
-    elapsed, e2e_s = r["elapsed"], (r["e2e"] or {}).get("seconds")
-    elapsed, e2e_s, per_launch = max_over_ranks([elapsed, e2e_s or 0.0, r["per_launch"]], world)
+    # the other parts of the metric, each on this rank's GPU (replicas)
+    records = {}
+    if not args.no_records:
+        for name, rs in RECORDS.items():
+            rspec = dict(rs, chi0=args.chi0, window=args.window)
+            rr = run_grid(rspec, K, args.warmup, rank, world, local_rank, False)
+            el, ps = max_over_ranks([rr["elapsed"], rr["per_step"]], world)
+            rr.update(elapsed=el, per_step=ps)
+            records[name] = (rspec, rr)
+    sweep = None
+    if not args.no_records and world == 1:
+        sweep = sweep_record(args)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
 
-    cfg, cells = r["cfg"], r["cells"]
-    K, S = args.steps, args.window
-    units = cells * S * K * world
-    value = units / elapsed
     peak, peak_kind = peaks()
-    bpc = bytes_per_cell(args.precision, args.scheme, args.noise, args.time_block)
-    lpw = launches_per_window(args.scheme, args.time_block, S)
-    kernel = "fused_kernel" if args.time_block == 2 else "step_kernel"
-    achieved = bpc * cells / per_launch / 1e9
-    rate = cells / per_launch  # cell-updates/s of the step kernels alone
-    sm_mhz = r["clocks"].get("sm_max_mhz") or 2070.0
-    alu = {"bound": "alu", "unit": "TFLOP/s",
-           "flops_per_cell_update": FLOPS_PER_CELL_UPDATE[args.scheme],
-           "achieved": FLOPS_PER_CELL_UPDATE[args.scheme] * rate / 1e12,
-           "peak": alu_peak_tflops(args.precision, sm_mhz),
-           "peak_kind": f"derived: {'128 FP32' if args.precision == 'f32' else '2 FP64'} multiply-adds "
-                        f"per SM and clock x {SMS} SMs x {sm_mhz:.0f} MHz"}
-    alu["frac"] = alu["achieved"] / alu["peak"]
-    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-           "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-           "kernel": kernel,
-           "traffic": kernel_traffic(args.precision, kernel, cfg["nx"], cfg["ny"], args.scheme,
-                                     args.noise),
-           "algorithmic_bytes_per_cell": bpc,
-           "kernel_ms_per_time_step": per_launch * 1e3,
-           # the HBM-roofline rate of a one-step-per-pass stepper
-           # (20 B per FP32 cell-update): temporal blocking may pass it
-           "one_step_pass_roofline_cell_updates_per_s":
-               peak * 1e9 / bytes_per_cell(args.precision, args.scheme, args.noise, 1),
-           "kernel_cell_updates_per_s": rate,
-           "launches_per_time_step": lpw / S}
-    if args.precision == "f64":
-        # the FP64 pass is bound by the FP64 pipe: that is its roofline
-        roofline = dict(alu, kernel=kernel, traffic=hbm["traffic"], kernel_cell_updates_per_s=rate,
-                        kernel_ms_per_time_step=per_launch * 1e3, hbm=hbm)
-    else:
-        roofline = dict(hbm, alu_fp32=alu)
-        if args.time_block == 2:
-            roofline["limiter"] = ("instruction issue: two stages per pass halve the HBM bytes "
-                                   "per cell-update, and the pass then issues about 58 thread "
-                                   "instructions per cell-update (ncu: issue slots 69 % busy, "
-                                   "1.5 eligible warps per cycle at 4 warps per scheduler)")
+    cells = r["cells"]
+    units = cells * args.window * K * world
+    line = grid_line(spec, r, K, world, peak, peak_kind, alu_peaks)
     out = {
         "metric": "grid-cell updates/s",
-        "value": value,
+        "value": line["value"],
         "unit": "cell-updates/s",
         "n_gpus": world,
         "steps": K,
         "warmup": args.warmup,
-        "ms_per_step": elapsed / K * 1e3,
+        "ms_per_step": line["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": args.precision,
         "data": "synthetic (seeded sigma field and Gaussian inoculum)",
-        "config": config_block(args, cfg),
-        "roofline": roofline,
-        "gpu_launches": K * (lpw + 2),
-        "clocks": r["clocks"],
-        "diagnostics_last": {k: r["diag"][k] for k in ("step", "t", "invariant", "r_env", "min_b", "min_n")},
+        "config": line["config"],
+        "roofline": line["roofline"],
+        "gpu_launches": line["gpu_launches"],
+        "clocks": line["clocks"],
+        "diagnostics_last": line["diagnostics_last"],
+        "alu_peaks_measured": {"f64_tflops": alu_peaks["f64"] / 1e12,
+                               "f32_tflops": alu_peaks["f32"] / 1e12,
+                               "how": "cx_alu_peak: 8 independent multiply-add chains per thread, "
+                                      "4 blocks of 256 threads per SM, best of 5, CUDA events"},
     }
     if r["e2e"]:
         out["e2e"] = {"value": units / e2e_s, "unit": "cell-updates/s",
@@ -459,17 +663,40 @@ def main():
                       "how": "cx_stage_state (b, n from pinned host memory, overlapping the "
                              "previous step), cx_commit_state, cx_step, cx_diagnostics "
                              "(device-to-host read) every step; host wall clock"}
-    if not args.no_cpu_baseline and world == 1:
-        v, sec, sample = cpu_baseline_sample(cfg)
+    cpu_leg = not args.no_cpu_baseline and world == 1
+    if records or sweep:
+        out["records"] = {}
+        for name, (rspec, rr) in records.items():
+            rec = grid_line(rspec, rr, K, world, peak, peak_kind, alu_peaks)
+            rec["metric"] = "grid-cell updates/s"
+            if cpu_leg:
+                rec["oracle_error"] = oracle_error_grid(rspec)
+            out["records"][name] = rec
+        if sweep:
+            if cpu_leg:
+                sweep["oracle_error"] = oracle_error_sweep(sweep["config"]["tuning"])
+            out["records"]["sweep_512"] = sweep
+    if cpu_leg:
+        out["oracle_error"] = oracle_error_grid(spec)
+        v, sec, sample = cpu_baseline_sample(r["cfg"])
         out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                                "sample": sample}
+        try:
+            import oracle
+            threads = os.cpu_count() or 1
+            v, sec, sample = cpu_baseline_sample(r["cfg"], steps=32, threads=threads)
+            out["cpu_baseline_all_cores"] = {"value": v, "unit": "cell-updates/s",
+                                             "cores": oracle.omp_threads(), "kind": "oracle",
+                                             "sample": sample}
+        except Exception as e:  # no OpenMP on this host: report why
+            out["cpu_baseline_all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
     print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def main_sweep(args):
+def sweep_record(args):
     """Batched parameter sweep (512 instances, sides 512..2048, FP32): sweep
     points per hour of the batch, and of the same points stepped one
     simulation at a time through cx_step (both measured in this run; each
@@ -492,10 +719,14 @@ def main_sweep(args):
     bt._stream = stream
     if args.tune:
         autotune.tune_batch(bt, steps=64, reps=2, use_cache=False)
+    else:
+        # the autotuner's choice on this sweep (128-row tiles, 64-step graphs,
+        # two stages per pass), fixed so that the default run needs no search
+        bt.tune(128, 64, 0, 0, 2)
     choice = cx.cx_batch_get_tuning(bt.h)
     depth = cx.cx_batch_get_time_block(bt.h)
 
-    def timed(step_fn, diag_fn, clk=None):
+    def timed(step_fn, diag_fn):
         for _ in range(Wm):
             step_fn(S)
             diag_fn()
@@ -513,8 +744,7 @@ def main_sweep(args):
         stop.synchronize()
         return start.elapsed_time(stop) / 1e3, sum(a.elapsed_time(b) for a, b in evs) / 1e3
 
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
-    with ClockSampler(uuid) as clk:
+    with ClockSampler(gpu_uuid(torch.device("cuda", torch.cuda.current_device()))) as clk:
         elapsed, kernel_s = timed(bt.step, bt.diagnostics)
     per_step = elapsed / (K * S)
     batch_pph = args.count * 3600.0 / (args.point_steps * per_step + create_s)
@@ -540,15 +770,15 @@ def main_sweep(args):
     achieved = bpc * cells / (kernel_s / (K * S)) / 1e9
     tuning = {"tile_rows": choice[0], "graph_steps": choice[1], "group_bytes": choice[2],
               "resident_steps": choice[3], "time_block": depth}
-    print(json.dumps({
-        "metric": "sweep points/hour", "value": batch_pph, "unit": "points/h", "n_gpus": 1,
-        "steps": K, "warmup": Wm, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {
+        "metric": "sweep points/hour", "value": batch_pph, "unit": "points/h",
+        "ms_per_step": elapsed / K * 1e3, "dtype": "f32",
         "config": {"workload": f"batched sweep: {args.count} instances, sides from "
                                f"{sorted(set(s['nx'] for s in specs))}, (n0, chi0, sigma0) log grid, "
                                f"static uniform noise a=0.5, forward Euler, {args.point_steps} steps "
                                f"per point", "cells_per_time_step": cells,
-                   "time_steps_per_step": S, "tuning": tuning},
+                   "time_steps_per_step": S, "tuning": tuning,
+                   "l2": "inputs larger than L2 (20 GB of state); no flush"},
         "cell_updates_per_s": cells / per_step,
         "single_instance_points_per_hour": single_pph,
         "single_instance_ms_per_time_step": {str(k): v[0] * 1e3 for k, v in single.items()},
@@ -560,7 +790,7 @@ def main_sweep(args):
                      "algorithmic_bytes_per_cell": bpc},
         "gpu_launches": K * (launches_per_window("euler", depth, S) + 2),
         "clocks": clk.summary(),
-    }))
+    }
 
 
 def main_reference(args, rank, world):

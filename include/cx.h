@@ -411,23 +411,47 @@ void cx_mlp_destroy(cx_mlp *m);
  *               dt are 0: there is no handle).  If NULL the call only
  *               queues work on `stream` and returns.
  * The per-block partial records live in one static device array of 1024
- * records x 8 doubles (64 KiB), which every GPU that loads the library holds
- * until the process exits.  The reduction uses at most 1024 blocks for any
- * grid, so every grid within the library's limits fits: nx, ny >= 1,
- * nx*ny <= 2^32 and ny <= 2,097,120; larger sizes are rejected with
- * CX_ERR_INVALID_ARG.  The call allocates nothing and frees nothing.
+ * records x 8 doubles (64 KiB).  The CUDA driver sets the array up when it
+ * loads the library's device code on a device: at the first call on that
+ * device under lazy module loading (CUDA's default), or when the library is
+ * loaded if CUDA_MODULE_LOADING=EAGER; from then on the device holds it
+ * until the process exits (or its context is destroyed).  That first call
+ * per device may therefore make the driver allocate the module's memory;
+ * every later call allocates nothing and frees nothing.  The reduction uses
+ * at most 1024 blocks for any grid, so every grid within these limits fits:
+ * nx, ny >= 1, nx*ny <= 2^32, nx <= 2^26 (so that record slot 5 holds the
+ * squared radius exactly, below 2^53) and ny <= 2,097,120; larger sizes are
+ * rejected with CX_ERR_INVALID_ARG.
  *
  * All calls share that one array and it keeps the last call's contents;
  * every record a call reads is written earlier in the same call, so nothing
  * needs clearing.  Calls that overlap on the GPU (on different streams, or
  * from different threads) race on the array and must be serialised by the
- * caller.  The first call on each device looks up the array's device
- * address (with that device current); make that first call before any
- * stream capture.  Errors: INVALID_ARG, CUDA, and NONFINITE / NEGATIVE
- * (with *out filled) as for cx_diagnostics when `out` is given. */
+ * caller.  The first call in each device's context looks up the array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  After cudaDeviceReset (or any destruction of the
+ * device's primary context) the next call looks the address up again in
+ * the new context, so it counts as a first call once more.  Errors:
+ * INVALID_ARG, CUDA, and NONFINITE / NEGATIVE (with *out filled) as for
+ * cx_diagnostics when `out` is given. */
 int cx_diagnostics_noalloc(const void *b, const void *n, int32_t nx, int32_t ny, int64_t pitch,
                            int32_t precision, double dx, double theta, double b_threshold,
                            void *stream, double *result_dev, cx_diag *out);
+
+/* ---- arithmetic peak of the device --------------------------------------- */
+
+/* The paper has no counterpart to this call: it measures the denominator of
+ * the step kernels' arithmetic roofline.  GB300 runs FP64 at a small
+ * fraction of its FP32 rate, so an FP64 state is bound by the FP64 pipe and
+ * its roofline needs that pipe's measured rate.  The call launches, on a
+ * private stream of the current device, a register-only kernel in which
+ * every thread advances 8 independent multiply-add chains (4 blocks of 256
+ * threads per SM), once to warm up and then `repeats` times (1..100), timed
+ * with CUDA events, and writes the best rate to *flops_per_s (a
+ * multiply-add counts two flops).  precision: CX_PREC_F64 or CX_PREC_F32.
+ * It allocates and frees one small device buffer and synchronises its
+ * stream.  Errors: INVALID_ARG, CUDA. */
+int cx_alu_peak(int32_t precision, int32_t repeats, double *flops_per_s);
 
 #ifdef __cplusplus
 }

@@ -23,8 +23,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cx_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "libcx_oracle.so")
+_OMP_LIB_PATH = os.path.join(_HERE, "libcx_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -34,27 +36,32 @@ _PD = ctypes.POINTER(ctypes.c_double)
 _PU32 = ctypes.POINTER(ctypes.c_uint32)
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, omp: bool = False) -> str:
     """Compile cx_oracle.c into libcx_oracle.so next to it (gcc, -O2,
-    -ffp-contract=off so no multiply-add is fused on any host)."""
+    -ffp-contract=off so no multiply-add is fused on any host); with omp,
+    the threaded build libcx_oracle_omp.so (-fopenmp: the row loop of the
+    right-hand side and the update loops on several host threads, the same
+    arithmetic per cell)."""
+    path = _OMP_LIB_PATH if omp else _LIB_PATH
     with _lock:
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-            return _LIB_PATH
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        if (not force and os.path.exists(path)
+                and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+            return path
+        tmp = path + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+               "-fPIC", "-shared"] + (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-        return _LIB_PATH
+        os.replace(tmp, path)
+        return path
 
 
-def _load():
-    global _lib
-    if _lib is not None:
+def _load(omp: bool = False):
+    global _lib, _omp_lib
+    if omp and _omp_lib is not None:
+        return _omp_lib
+    if not omp and _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_LIB_PATH)
+    lib = ctypes.CDLL(build(omp=omp))
     lib.orc_philox4x32_10.argtypes = [_PU32, _PU32, _PU32]
     lib.orc_philox4x32_10.restype = None
     lib.orc_noise_delta.argtypes = [_U64, _U64, _U64, _I]
@@ -78,7 +85,14 @@ def _load():
     lib.orc_diagnostics.restype = _I
     lib.orc_dt_limit.argtypes = [_D, _D, _D, _D, _D, _D, _D, _D]
     lib.orc_dt_limit.restype = _D
-    _lib = lib
+    lib.orc_threads.argtypes = []
+    lib.orc_threads.restype = _I
+    lib.orc_set_threads.argtypes = [_I]
+    lib.orc_set_threads.restype = None
+    if omp:
+        _omp_lib = lib
+    else:
+        _lib = lib
     return lib
 
 
@@ -159,15 +173,20 @@ def step(sigma, b, n, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0, schem
 
 
 def run(sigma, b, n, nsteps, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0,
-        scheme=0, noise_mode=0, seed=0, sigma0=0.0, amp=0.0, dist=0, step0=0, recipe=0):
+        scheme=0, noise_mode=0, seed=0, sigma0=0.0, amp=0.0, dist=0, step0=0, recipe=0,
+        threads=0):
     """Advance (b, n) by `nsteps` steps in place (copies are returned).  With
     noise_mode 1 sigma is redrawn from (seed, cell, m) before every step m,
-    by the FP64 recipe (recipe 0) or the FP32 recipe (recipe 1)."""
+    by the FP64 recipe (recipe 0) or the FP32 recipe (recipe 1).  threads >
+    0 runs the threaded build on that many host threads (same bits)."""
     s = np.array(sigma, np.float64, order="C", copy=True)
     bb = np.array(b, np.float64, order="C", copy=True)
     nn = np.array(n, np.float64, order="C", copy=True)
     ny, nx = bb.shape
-    rc = _load().orc_run(nx, ny, dx, dt, Dn, theta, chi0, chemo_law, mobility, scheme,
+    lib = _load(omp=threads > 0)
+    if threads > 0:
+        lib.orc_set_threads(int(threads))
+    rc = lib.orc_run(nx, ny, dx, dt, Dn, theta, chi0, chemo_law, mobility, scheme,
                          noise_mode, recipe, seed, sigma0, amp, dist, step0, nsteps,
                          _ptr(s), _ptr(bb), _ptr(nn))
     if rc != 0:
@@ -176,6 +195,12 @@ def run(sigma, b, n, nsteps, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0
 
 
 DIAG_KEYS = ("mass_b", "mass_n", "invariant", "min_b", "min_n", "max_b", "r_env", "finite")
+
+
+def omp_threads() -> int:
+    """Threads the threaded build uses by default (the host's cores, or
+    OMP_NUM_THREADS)."""
+    return int(_load(omp=True).orc_threads())
 
 
 def diagnostics(b, n, *, dx, theta, b_th) -> dict:

@@ -140,6 +140,8 @@ _SIGNATURES = {
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _P, _P,
                                               ctypes.POINTER(cx_diag)]),
+    "cx_alu_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -512,6 +514,14 @@ def cx_diagnostics_noalloc(b_ptr, n_ptr, nx, ny, pitch, precision, dx, theta, b_
     if rc not in (CX_OK, CX_ERR_NONFINITE, CX_ERR_NEGATIVE) or not want_host:
         _check(rc)
     return d
+
+
+def cx_alu_peak(precision, repeats=5) -> float:
+    """Measured multiply-add rate (FLOP/s, a multiply-add counting two) of
+    the current device in CX_PREC_F64 or CX_PREC_F32."""
+    v = ctypes.c_double()
+    _check(lib().cx_alu_peak(precision, repeats, ctypes.byref(v)))
+    return v.value
 
 
 # ---- convenience wrapper -----------------------------------------------------

@@ -169,6 +169,12 @@ int alloc_ctx(const cx_grid *g, const cx_params *p, uint64_t seed, double dt, cx
     c->time_block = c->prec == CX_PREC_F32 ? 2 : 1;
     c->stream = nullptr;
     cudaGetDevice(&c->device);
+    c->num_sms = 0;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        c->num_sms < 1) {
+        cudaGetLastError();
+        c->num_sms = 1;  // only the automatic tile height uses it
+    }
     const size_t bytes = (size_t)c->pitch * (size_t)g->ny * c->elem;
     cudaError_t e = cudaSuccess;
     if (ext) {
@@ -318,7 +324,8 @@ static int auto_tile_rows(const cx_ctx *c)
     const long long cap = two ? 64 : 32;
     const long long per_sm = two ? 8 : 4;
     const long long tiles_x = ((long long)c->g.nx + cols - 1) / cols;
-    long long rows = ((long long)c->g.ny * tiles_x + per_sm * 152 - 1) / (per_sm * 152);
+    const long long sms = c->num_sms;
+    long long rows = ((long long)c->g.ny * tiles_x + per_sm * sms - 1) / (per_sm * sms);
     rows = rows < 1 ? 1 : (rows > cap ? cap : rows);
     while (((long long)c->g.ny + rows - 1) / rows > 65535) ++rows;
     return (int)rows;

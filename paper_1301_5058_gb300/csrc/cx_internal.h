@@ -142,6 +142,7 @@ struct cx_ctx {
     double dt;
     cudaStream_t stream;
     int device;
+    int num_sms;          // streaming multiprocessors of that device
     int tile_rows;        // rows per step-kernel tile (0: automatic)
     int time_block;       // explicit stages per pass over the grid (1 or 2)
     cx::DiagScratch diag;

@@ -5,12 +5,16 @@
 // The kernels are the ones cx_diagnostics launches (cx_diag.cu); only the
 // home of their per-block partial records differs.  In host code the name
 // g_diag_scratch is a host-side stand-in, not a device address, so the
-// address is looked up once per device with cudaGetSymbolAddress and passed
-// to the launcher.
+// address is looked up with cudaGetSymbolAddress, with the device current,
+// and passed to the launcher.  The lookup is cached per device and per CUDA
+// context: a context that is destroyed and created again (cudaDeviceReset)
+// loads the module again, possibly at another address, and gets a fresh
+// lookup.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <cuda.h>
 #include <mutex>
 
 #include "cx_internal.h"
@@ -19,11 +23,51 @@ namespace {
 
 constexpr int kScratchRecords = 1024;  // the reduction never uses more blocks
 constexpr int kMaxDevices = 64;
+// widest grid whose squared envelope radius (2i+1-nx)^2 + (2j+1-ny)^2 stays
+// below 2^53, so that the record's slot 5 holds it exactly: (2^26)^2 = 2^52
+// and, with ny <= 2,097,120 < 2^21, (2^21)^2 = 2^42
+constexpr long long kMaxNx = 1LL << 26;
 
 static __device__ __align__(256) double g_diag_scratch[kScratchRecords * 8];
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+struct Cached {
+    unsigned long long ctx_id;  // 0: none
+    void *addr;
+};
+
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+Cached g_cache[kMaxDevices] = {};
+bool g_fns_tried = false;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// The unique id of the current context (0 if there is none, or if the
+// driver cannot tell: then nothing is cached).  Called with g_mu held.
+unsigned long long current_ctx_id()
+{
+    if (!g_fns_tried) {
+        g_fns_tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -36,8 +80,10 @@ static int noalloc_fail(int code, const char *msg, const char *detail)
     return cx::record_error(code, buf);
 }
 
-// Device address of the scratch array on the current device (looked up
-// once per device, with that device current).
+// Device address of the scratch array in the current device's context.  The
+// first call in a context looks it up (and, under lazy module loading, makes
+// the driver load this file's module, which holds the array); later calls in
+// the same context reuse it.
 static int scratch_address(double **out)
 {
     int dev = -1;
@@ -45,14 +91,19 @@ static int scratch_address(double **out)
     if (e != cudaSuccess) return noalloc_fail(CX_ERR_CUDA, "cudaGetDevice", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(CX_ERR_CUDA, "device index out of range", nullptr);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_diag_scratch);
-        if (e != cudaSuccess || !p)
-            return noalloc_fail(CX_ERR_CUDA, "cudaGetSymbolAddress", cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+    const unsigned long long id = current_ctx_id();
+    if (id != 0 && g_cache[dev].ctx_id == id) {
+        *out = (double *)g_cache[dev].addr;
+        return CX_OK;
     }
-    *out = (double *)g_scratch_addr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_diag_scratch);
+    if (e != cudaSuccess || !p)
+        return noalloc_fail(CX_ERR_CUDA, "cudaGetSymbolAddress", cudaGetErrorString(e));
+    // the lookup made the device's primary context current if it was not
+    g_cache[dev].ctx_id = current_ctx_id();
+    g_cache[dev].addr = p;
+    *out = (double *)p;
     return CX_OK;
 }
 
@@ -65,9 +116,10 @@ extern "C" int cx_diagnostics_noalloc(const void *b, const void *n, int32_t nx, 
         return noalloc_fail(CX_ERR_INVALID_ARG, "b, n and result_dev must not be NULL", nullptr);
     if (nx < 1 || ny < 1 || pitch < nx)
         return noalloc_fail(CX_ERR_INVALID_ARG, "need nx, ny >= 1 and pitch >= nx", nullptr);
-    if ((long long)nx * ny > (1LL << 32) || ny > 65535LL * 32)
+    if ((long long)nx * ny > (1LL << 32) || ny > 65535LL * 32 || nx > kMaxNx)
         return noalloc_fail(CX_ERR_INVALID_ARG,
-                            "grid exceeds the maximum (nx*ny <= 2^32, ny <= 2097120)", nullptr);
+                            "grid exceeds the maximum (nx*ny <= 2^32, nx <= 2^26, ny <= 2097120)",
+                            nullptr);
     if (precision != CX_PREC_F64 && precision != CX_PREC_F32)
         return noalloc_fail(CX_ERR_INVALID_ARG, "precision must be CX_PREC_F64 or CX_PREC_F32", nullptr);
     if (!(isfinite(dx) && dx > 0.0) || !(isfinite(theta) && theta >= 0.0) ||

@@ -73,7 +73,10 @@ __device__ __forceinline__ Acc block_reduce(Acc a)
 __device__ __forceinline__ void store_acc(double *dst, const Acc &a)
 {
     dst[0] = a.sb; dst[1] = a.sn; dst[2] = a.mnb; dst[3] = a.mnn; dst[4] = a.mxb;
-    dst[5] = (double)a.r2;  // exact: below 2^53
+    // exact while r2 < 2^53, i.e. for nx <= 2^26 (ny is at most 2,097,120);
+    // a wider grid rounds it to the nearest double, a relative change below
+    // 2^-53 (no overflow: |2i+1-nx| < 2^31)
+    dst[5] = (double)a.r2;
     dst[6] = (double)a.bad;
     dst[7] = 0.0;
 }

@@ -544,3 +544,21 @@ def test_c_star_below_c_bar_and_increasing_in_chi0():
         assert cs[-1] < speed.c_bar(n0, chi0, sigma0)
         assert speed.mm_bound(D, g, 20001) == pytest.approx(speed.c_bar(n0, chi0, sigma0), rel=1e-6)
     assert cs[1] > cs[0]
+
+
+# ---------------------------------------------------------------------------
+# Threaded build of the oracle (timed as the all-cores CPU baseline)
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_threaded_oracle_gives_the_same_bits(scheme):
+    # only the row loop of the right-hand side and the update loops are split
+    # across threads; each cell's arithmetic is unchanged, so the results are
+    # identical to the serial build's
+    nx, ny = 97, 61
+    s = oracle.sigma_field(nx, ny, 4, 4.0, 0.5)
+    b, n = oracle.initial_state(nx, ny, 1.0, 0.7, 0.5, 16.0)
+    kw = dict(dx=1.0, dt=0.006, Dn=1.0, theta=1.0, chi0=1.5, scheme=scheme)
+    b1, n1, _ = oracle.run(s, b, n, 40, **kw)
+    b4, n4, _ = oracle.run(s, b, n, 40, threads=4, **kw)
+    assert np.array_equal(b1, b4) and np.array_equal(n1, n4)
+    assert oracle.omp_threads() >= 1

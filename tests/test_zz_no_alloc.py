@@ -71,12 +71,43 @@ def test_noalloc_matches_cx_diagnostics_on_two_calls_in_a_row(cx, prec):
         assert rec[2] == ref["min_b"] and rec[4] == ref["max_b"]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_calls_after_the_first_allocate_no_device_memory(cx, prec):
+    # The property the entry point exists for: once the first call on the
+    # device has set its scratch array up, further calls leave both the
+    # caller's allocator and the device's free memory exactly as they were.
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.float64 if prec == cx.CX_PREC_F64 else torch.float32
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    nx, ny = 1000, 777
+    ref, b, n = _state(cx, nx, ny, prec, 200, 3)
+    bd = torch.from_numpy(b).to(dev)
+    nd = torch.from_numpy(n).to(dev)
+    result = torch.zeros(8, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    args = (bd.data_ptr(), nd.data_ptr(), nx, ny, nx, prec, 1.0, 1.0, 0.1 * W.CONFIG0["n0"], stream,
+            result.data_ptr())
+    cx.cx_diagnostics_noalloc(*args)  # warm-up: the first call may set the array up
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
+    for _ in range(2):
+        d = cx.cx_diagnostics_noalloc(*args).as_dict()
+        _compare(d, ref)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
+    assert after == before
+
+
 def test_noalloc_rejects_bad_sizes(cx):
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", torch.cuda.current_device())
     buf = torch.zeros(64, dtype=torch.float64, device=dev)
     p = buf.data_ptr()
-    for nx, ny, pitch in ((0, 4, 4), (4, 0, 4), (8, 4, 7), (70000, 70000, 70000), (1, 3000000, 1)):
+    # the last case: wider than 2^26 columns, where the squared envelope radius
+    # in record slot 5 would no longer be exact
+    for nx, ny, pitch in ((0, 4, 4), (4, 0, 4), (8, 4, 7), (70000, 70000, 70000), (1, 3000000, 1),
+                          ((1 << 26) + 1, 1, (1 << 26) + 1)):
         with pytest.raises(cx.CxError) as e:
             cx.cx_diagnostics_noalloc(p, p, nx, ny, pitch, 0, 1.0, 1.0, 0.1, None, p)
         assert e.value.code == cx.CX_ERR_INVALID_ARG
