@@ -270,13 +270,19 @@ void cx_destroy(cx_ctx *c);
  * A batch holds `count` independent simulations of the same system with
  * their own grid size, parameters (n0, chi0, sigma0, a, ...) and seed, as in
  * the parameter study of Sec. 3 (Table tabresparam).  All instances share
- * precision, scheme, chemo_law and mobility; noise must be CX_NOISE_STATIC.
- * An instance evolves bit for bit as a cx_ctx created with the same grid,
- * parameters and seed.  A batch owns a non-default CUDA stream. */
+ * precision, scheme, chemo_law, mobility and noise_mode.  With
+ * CX_NOISE_PER_STEP (the paper's own runs, Sec. 3: sigma redrawn at every
+ * point and time step) each instance draws sigma from (its seed, cell, time
+ * step) as a single grid does; the batch keeps the time step in a device
+ * word that it writes before each captured graph or run of passes, so the
+ * graphs stay valid across calls.  An instance evolves bit for bit as a
+ * cx_ctx created with the same grid, parameters and seed.  A batch owns a
+ * non-default CUDA stream. */
 
 /* Allocate and initialise `count` instances (1..65535); grids[i],
  * params[i], seeds[i] describe instance i.  Synchronous.  Errors:
- * INVALID_ARG, DT_UNSTABLE, UNSUPPORTED (per-step noise), OOM, CUDA. */
+ * INVALID_ARG (including instances that differ in precision, scheme,
+ * chemo_law, mobility or noise_mode), DT_UNSTABLE, OOM, CUDA. */
 int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params,
                     const uint64_t *seeds, cx_batch **out);
 

@@ -37,13 +37,16 @@ namespace batch {
 // defined in cx_batch_kernels.cuh, instantiated in cx_batch_inst.cu
 template <typename T, int LAW, int MOB>
 cudaError_t launch_step_lm(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                           int stage, cudaStream_t st);
+                           int stage, int noise, const long long *step_base, int step_off,
+                           cudaStream_t st);
 template <typename T, int LAW, int MOB>
 cudaError_t launch_fused_lm(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                            int heun, cudaStream_t st);
+                            int heun, int noise, const long long *step_base, int step_off,
+                            cudaStream_t st);
 template <typename T, int LAW, int MOB>
 cudaError_t launch_resident_lm(const void *inst, const int4 *work, int nwork, int parity,
-                               int rows, int nsteps, int heun, void *gb, long long spin,
+                               int rows, int nsteps, int heun, int noise, void *gb,
+                               long long spin, const long long *step_base, int step_off,
                                cudaStream_t st);
 }  // namespace batch
 
@@ -84,45 +87,45 @@ __global__ void __launch_bounds__(reduce::kThreads)
     if (threadIdx.x == 0) reduce::store_acc(out + 8LL * i, a);
 }
 
+// (law, mobility) of a run -> the instantiation that serves it
+#define CX_BATCH_DISPATCH(FN, ...)                                                          \
+    (law == CX_CHEMO_RECEPTOR                                                               \
+         ? (mob == CX_MOBILITY_CENTRAL                                                      \
+                ? batch::FN<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(__VA_ARGS__)          \
+                : batch::FN<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(__VA_ARGS__))          \
+         : (mob == CX_MOBILITY_CENTRAL                                                      \
+                ? batch::FN<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(__VA_ARGS__)          \
+                : batch::FN<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(__VA_ARGS__)))
+
 template <typename T>
 cudaError_t launch_fused_prec(int law, int mob, const void *inst, const int4 *work, int nwork,
-                              int parity, int rows, int heun, cudaStream_t st)
+                              int parity, int rows, int heun, const BatchNoise &nz, cudaStream_t st)
 {
-    if (law == CX_CHEMO_RECEPTOR)
-        return mob == CX_MOBILITY_CENTRAL
-                   ? batch::launch_fused_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, heun, st)
-                   : batch::launch_fused_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, heun, st);
-    return mob == CX_MOBILITY_CENTRAL
-               ? batch::launch_fused_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, heun, st)
-               : batch::launch_fused_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, heun, st);
+    return CX_BATCH_DISPATCH(launch_fused_lm, inst, work, nwork, parity, rows, heun, nz.on,
+                             nz.step_base, nz.step_off, st);
 }
 
 template <typename T>
 cudaError_t launch_batch_prec(int law, int mob, const void *inst, const int4 *work, int nwork,
-                              int parity, int rows, int stage, cudaStream_t st)
+                              int parity, int rows, int stage, const BatchNoise &nz, cudaStream_t st)
 {
-    if (law == CX_CHEMO_RECEPTOR)
-        return mob == CX_MOBILITY_CENTRAL
-                   ? batch::launch_step_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, stage, st)
-                   : batch::launch_step_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, stage, st);
-    return mob == CX_MOBILITY_CENTRAL
-               ? batch::launch_step_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, stage, st)
-               : batch::launch_step_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, stage, st);
+    return CX_BATCH_DISPATCH(launch_step_lm, inst, work, nwork, parity, rows, stage, nz.on,
+                             nz.step_base, nz.step_off, st);
 }
 
 template <typename T>
 cudaError_t launch_resident_prec(int law, int mob, const void *inst, const int4 *work, int nwork,
                                  int parity, int rows, int nsteps, int heun, void *gb, long long spin,
-                                 cudaStream_t st)
+                                 const BatchNoise &nz, cudaStream_t st)
 {
-    if (law == CX_CHEMO_RECEPTOR)
-        return mob == CX_MOBILITY_CENTRAL
-                   ? batch::launch_resident_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st)
-                   : batch::launch_resident_lm<T, CX_CHEMO_RECEPTOR, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st);
-    return mob == CX_MOBILITY_CENTRAL
-               ? batch::launch_resident_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_CENTRAL>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st)
-               : batch::launch_resident_lm<T, CX_CHEMO_CONSTANT, CX_MOBILITY_UPWIND>(inst, work, nwork, parity, rows, nsteps, heun, gb, spin, st);
+    return CX_BATCH_DISPATCH(launch_resident_lm, inst, work, nwork, parity, rows, nsteps, heun,
+                             nz.on, gb, spin, nz.step_base, nz.step_off, st);
 }
+
+#undef CX_BATCH_DISPATCH
+
+// Writes the time step the next batch pass starts from (per-step noise).
+__global__ void set_step_kernel(long long *p, long long v) { *p = v; }
 
 }  // namespace
 
@@ -130,27 +133,36 @@ size_t grid_barrier_bytes() { return sizeof(GridBarrier); }
 
 cudaError_t launch_batch_resident(int prec, int law, int mob, const void *inst, const int4 *work,
                                   int nwork, int parity, int rows, int nsteps, int heun,
-                                  void *barrier, long long spin_limit, cudaStream_t st)
+                                  void *barrier, long long spin_limit, const BatchNoise &nz,
+                                  cudaStream_t st)
 {
     return prec == CX_PREC_F64
-               ? launch_resident_prec<double>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, st)
-               : launch_resident_prec<float>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, st);
+               ? launch_resident_prec<double>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, nz, st)
+               : launch_resident_prec<float>(law, mob, inst, work, nwork, parity, rows, nsteps, heun, barrier, spin_limit, nz, st);
 }
 
 cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, const int4 *work,
-                              int nwork, int parity, int rows, int stage, cudaStream_t st)
+                              int nwork, int parity, int rows, int stage, const BatchNoise &nz,
+                              cudaStream_t st)
 {
     return prec == CX_PREC_F64
-               ? launch_batch_prec<double>(law, mob, inst, work, nwork, parity, rows, stage, st)
-               : launch_batch_prec<float>(law, mob, inst, work, nwork, parity, rows, stage, st);
+               ? launch_batch_prec<double>(law, mob, inst, work, nwork, parity, rows, stage, nz, st)
+               : launch_batch_prec<float>(law, mob, inst, work, nwork, parity, rows, stage, nz, st);
 }
 
 cudaError_t launch_batch_fused(int prec, int law, int mob, const void *inst, const int4 *work,
-                               int nwork, int parity, int rows, int heun, cudaStream_t st)
+                               int nwork, int parity, int rows, int heun, const BatchNoise &nz,
+                               cudaStream_t st)
 {
     return prec == CX_PREC_F64
-               ? launch_fused_prec<double>(law, mob, inst, work, nwork, parity, rows, heun, st)
-               : launch_fused_prec<float>(law, mob, inst, work, nwork, parity, rows, heun, st);
+               ? launch_fused_prec<double>(law, mob, inst, work, nwork, parity, rows, heun, nz, st)
+               : launch_fused_prec<float>(law, mob, inst, work, nwork, parity, rows, heun, nz, st);
+}
+
+cudaError_t launch_set_step(long long *step_base, long long step, cudaStream_t st)
+{
+    set_step_kernel<<<1, 1, 0, st>>>(step_base, step);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,
@@ -175,7 +187,8 @@ size_t inst_dev_bytes(int prec) { return prec == CX_PREC_F64 ? sizeof(InstDev<do
 
 // Host-side fill of one table entry (the table is copied to the device whole).
 void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void *n1, void *s,
-               int nx, int ny, long long pitch, const Coef &k, double bth)
+               int nx, int ny, long long pitch, const Coef &k, double bth, uint64_t seed,
+               double sigma0, double amp, int dist)
 {
     if (prec == CX_PREC_F64) {
         InstDev<double> &d = ((InstDev<double> *)table)[i];
@@ -185,6 +198,10 @@ void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void 
         d.k = CoefT<double>{k.cA, k.cChi, k.cG, k.cR, k.cN};
         d.fth = reduce::float_threshold(bth);
         d.bth = bth;
+        d.seed = seed;
+        d.sigma0 = sigma0;
+        d.amp = amp;
+        d.dist = dist;
     } else {
         InstDev<float> &d = ((InstDev<float> *)table)[i];
         d.b[0] = (float *)b0; d.b[1] = (float *)b1; d.n[0] = (float *)n0; d.n[1] = (float *)n1;
@@ -193,6 +210,10 @@ void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void 
         d.k = CoefT<float>{(float)k.cA, (float)k.cChi, (float)k.cG, (float)k.cR, (float)k.cN};
         d.fth = reduce::float_threshold(bth);
         d.bth = bth;
+        d.seed = seed;
+        d.sigma0 = (float)sigma0;
+        d.amp = (float)amp;
+        d.dist = dist;
     }
 }
 

@@ -37,6 +37,8 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct cx_batch {
     int count = 0, prec = 0, law = 0, mob = 0, scheme = 0;
+    int noise = 0;                  // 1: sigma redrawn every step (CX_NOISE_PER_STEP)
+    long long *d_step = nullptr;    // time step the next pass starts from (noise == 1)
     std::vector<cx_grid> g;
     std::vector<cx_params> p;
     std::vector<uint64_t> seed;
@@ -94,6 +96,7 @@ void free_batch(cx_batch *B)
     if (B->d_res) cudaFree(B->d_res);
     if (B->h_res) cudaFreeHost(B->h_res);
     if (B->d_barrier) cudaFree(B->d_barrier);
+    if (B->d_step) cudaFree(B->d_step);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
     delete B;
 }
@@ -143,38 +146,56 @@ void build_groups(cx_batch *B)
     B->group_first.push_back(B->count);
 }
 
-// One time step of instances [i0, i1) at the given parity; returns the parity after.
-cudaError_t one_step(cx_batch *B, int i0, int i1, int parity)
+// The noise argument of a pass whose first time step is step_off after the
+// step last written to d_step.
+cx::BatchNoise pass_noise(const cx_batch *B, int step_off)
+{
+    return cx::BatchNoise{B->noise, B->d_step, step_off};
+}
+
+// Before the passes (or the graph) that start at time step `step`: where the
+// per-step noise reads its step from.
+cudaError_t mark_step(cx_batch *B, int64_t step)
+{
+    return B->noise ? cx::launch_set_step(B->d_step, (long long)step, B->stream) : cudaSuccess;
+}
+
+// One time step of instances [i0, i1) at the given parity, step_off steps
+// after the marked step.
+cudaError_t one_step(cx_batch *B, int i0, int i1, int parity, int step_off)
 {
     const int w0 = B->work_begin[i0], w1 = B->work_begin[i1];
     const int4 *work = B->d_work + w0;
+    const cx::BatchNoise nz = pass_noise(B, step_off);
     cudaError_t e = cx::launch_batch_step(B->prec, B->law, B->mob, B->d_inst, work, w1 - w0,
-                                          parity, B->rows, 0, B->stream);
+                                          parity, B->rows, 0, nz, B->stream);
     if (e == cudaSuccess && B->scheme == CX_SCHEME_HEUN)
         e = cx::launch_batch_step(B->prec, B->law, B->mob, B->d_inst, work, w1 - w0, parity,
-                                  B->rows, 1, B->stream);
+                                  B->rows, 1, nz, B->stream);
     return e;
 }
 
 int next_parity(const cx_batch *B, int parity) { return B->scheme == CX_SCHEME_HEUN ? parity : parity ^ 1; }
 
-// One pass over instances [i0, i1) starting at *parity: two stages when the
-// depth is 2 (two Euler steps if at least two are left, or one Heun step),
-// else one step.  Sets *steps to the time steps taken and *parity to the
-// parity after them.
-cudaError_t one_pass(cx_batch *B, int i0, int i1, int *parity, int64_t left, int *steps)
+// One pass over instances [i0, i1) starting at *parity, step_off steps
+// after the marked step: two stages when the depth is 2 (two Euler steps if
+// at least two are left, or one Heun step), else one step.  Sets *steps to
+// the time steps taken and *parity to the parity after them.
+cudaError_t one_pass(cx_batch *B, int i0, int i1, int *parity, int64_t left, int step_off,
+                     int *steps)
 {
     const bool heun = B->scheme == CX_SCHEME_HEUN;
     if (B->time_block == 2 && (heun || left >= 2)) {
         const int w0 = B->work2_begin[i0], w1 = B->work2_begin[i1];
         const cudaError_t e = cx::launch_batch_fused(B->prec, B->law, B->mob, B->d_inst,
                                                      B->d_work2 + w0, w1 - w0, *parity, B->rows,
-                                                     heun ? 1 : 0, B->stream);
+                                                     heun ? 1 : 0, pass_noise(B, step_off),
+                                                     B->stream);
         *parity ^= 1;
         *steps = heun ? 1 : 2;
         return e;
     }
-    const cudaError_t e = one_step(B, i0, i1, *parity);
+    const cudaError_t e = one_step(B, i0, i1, *parity, step_off);
     *parity = next_parity(B, *parity);
     *steps = 1;
     return e;
@@ -190,7 +211,8 @@ int capture_group(cx_batch *B, int gi, int parity, cudaGraphExec_t *out, int *en
     int par = parity;
     for (int64_t left = B->graph_steps; left > 0 && e == cudaSuccess;) {
         int taken = 1;
-        e = one_pass(B, B->group_first[gi], B->group_first[gi + 1], &par, left, &taken);
+        e = one_pass(B, B->group_first[gi], B->group_first[gi + 1], &par, left,
+                     (int)(B->graph_steps - left), &taken);
         left -= taken;
     }
     cudaError_t e2 = cudaStreamEndCapture(B->stream, &graph);
@@ -224,18 +246,21 @@ int check_barrier(cx_batch *B)
     return CX_OK;
 }
 
-// `left` steps of instances [i0, i1) by cooperative launches of
-// resident_steps steps each; returns the parity after them.
-int run_resident(cx_batch *B, int i0, int i1, int par, int64_t left, int *par_out)
+// `left` steps of instances [i0, i1), the first of them time step `step`,
+// by cooperative launches of resident_steps steps each; returns the parity
+// after them.
+int run_resident(cx_batch *B, int i0, int i1, int par, int64_t left, int64_t step, int *par_out)
 {
     const int w0 = B->work_begin[i0], w1 = B->work_begin[i1];
     while (left > 0) {
         const int chunk = (int)(left < B->resident_steps ? left : B->resident_steps);
         BX_CUDA(cudaMemsetAsync(B->d_barrier, 0, 8, B->stream), "barrier reset");
+        BX_CUDA(mark_step(B, step), "step mark");
         BX_CUDA(cx::launch_batch_resident(B->prec, B->law, B->mob, B->d_inst, B->d_work + w0, w1 - w0,
                                           par, B->rows, chunk, B->scheme == CX_SCHEME_HEUN,
-                                          B->d_barrier, B->spin_limit, B->stream),
+                                          B->d_barrier, B->spin_limit, pass_noise(B, 0), B->stream),
                 "resident batch launch");
+        step += chunk;
         if (B->scheme == CX_SCHEME_EULER && (chunk & 1)) par ^= 1;
         left -= chunk;
     }
@@ -262,8 +287,6 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
             a.mobility != z.mobility || a.noise_mode != z.noise_mode)
             return bfail(CX_ERR_INVALID_ARG, "all instances of a batch must share precision, "
                                              "scheme, chemo_law, mobility and noise_mode");
-        if (a.noise_mode == CX_NOISE_PER_STEP)
-            return bfail(CX_ERR_UNSUPPORTED, "batches support static noise only");
     }
     cx_batch *B = new (std::nothrow) cx_batch;
     if (!B) return bfail(CX_ERR_OOM, "host allocation of the batch failed");
@@ -272,6 +295,7 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
     B->law = params[0].chemo_law;
     B->mob = params[0].mobility;
     B->scheme = params[0].scheme;
+    B->noise = params[0].noise_mode == CX_NOISE_PER_STEP ? 1 : 0;
     B->time_block = B->prec == CX_PREC_F32 ? 2 : 1;  // as a single grid
     B->elem = B->prec == CX_PREC_F64 ? sizeof(double) : sizeof(float);
     B->g.assign(grids, grids + count);
@@ -322,7 +346,8 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
     for (int i = 0; i < count; ++i)
         cx::fill_inst(B->prec, B->h_inst.data(), i, B->fb[0][i], B->fb[1][i], B->fn[0][i],
                       B->fn[1][i], B->fs[i], grids[i].nx, grids[i].ny, B->pitch[i],
-                      cx::make_coef(grids[i], params[i], B->dt[i]), cx::envelope_level(params[i]));
+                      cx::make_coef(grids[i], params[i], B->dt[i]), cx::envelope_level(params[i]),
+                      seeds[i], params[i].sigma0, params[i].noise_amp, params[i].noise_dist);
     e = cudaMalloc(&B->d_inst, B->h_inst.size());
     if (e == cudaSuccess) e = cudaMemcpy(B->d_inst, B->h_inst.data(), B->h_inst.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_part, 8 * sizeof(double) * (size_t)count * kDiagBlocksPerInst);
@@ -330,6 +355,8 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
     if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_res, 8 * sizeof(double) * (size_t)count);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_barrier, cx::grid_barrier_bytes());
     if (e == cudaSuccess) e = cudaMemset(B->d_barrier, 0, cx::grid_barrier_bytes());
+    if (e == cudaSuccess && B->noise) e = cudaMalloc((void **)&B->d_step, sizeof(long long));
+    if (e == cudaSuccess && B->noise) e = cudaMemset(B->d_step, 0, sizeof(long long));
     if (e != cudaSuccess) { cudaGetLastError(); free_batch(B); return bcuda(e, "batch tables"); }
     if (const char *s = getenv("CX_BARRIER_SPIN_LIMIT")) B->spin_limit = atoll(s);
     int rc = build_work(B);
@@ -442,7 +469,7 @@ int cx_batch_step(cx_batch *B, int64_t n_steps)
         int par = B->cur;
         int64_t left = n_steps;
         if (B->resident_steps > 0) {
-            rc = run_resident(B, i0, i1, par, left, &end_parity);
+            rc = run_resident(B, i0, i1, par, left, B->step, &end_parity);
             if (rc) return rc;
             continue;
         }
@@ -452,14 +479,20 @@ int cx_batch_step(cx_batch *B, int64_t n_steps)
                     rc = capture_group(B, gi, par, &B->gexec[par][gi], &B->gend[par][gi]);
                     if (rc) return rc;
                 }
+                BX_CUDA(mark_step(B, B->step + (n_steps - left)), "step mark");
                 BX_CUDA(cudaGraphLaunch(B->gexec[par][gi], B->stream), "graph launch");
                 left -= B->graph_steps;
                 par = B->gend[par][gi];
             }
         }
+        int64_t marked = -1;  // `left` when the step was last marked
         while (left > 0) {
+            if (marked < 0 || marked - left > (1 << 30)) {
+                BX_CUDA(mark_step(B, B->step + (n_steps - left)), "step mark");
+                marked = left;
+            }
             int taken = 1;
-            BX_CUDA(one_pass(B, i0, i1, &par, left, &taken), "batch step launch");
+            BX_CUDA(one_pass(B, i0, i1, &par, left, (int)(marked - left), &taken), "batch step launch");
             left -= taken;
         }
         end_parity = par;

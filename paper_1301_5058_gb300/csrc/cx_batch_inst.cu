@@ -10,12 +10,14 @@ namespace batch {
 
 #define CX_BATCH_INST(T, LAW, MOB)                                                             \
     template cudaError_t launch_step_lm<T, LAW, MOB>(const void *, const int4 *, int, int, int, \
-                                                     int, cudaStream_t);                       \
+                                                     int, int, const long long *, int,         \
+                                                     cudaStream_t);                            \
     template cudaError_t launch_fused_lm<T, LAW, MOB>(const void *, const int4 *, int, int,     \
-                                                      int, int, cudaStream_t);                 \
+                                                      int, int, int, const long long *, int,   \
+                                                      cudaStream_t);                           \
     template cudaError_t launch_resident_lm<T, LAW, MOB>(const void *, const int4 *, int, int,  \
-                                                         int, int, int, void *, long long,     \
-                                                         cudaStream_t);
+                                                         int, int, int, int, void *, long long, \
+                                                         const long long *, int, cudaStream_t);
 
 #if defined(CX_INST_PREC) && defined(CX_INST_LAW) && defined(CX_INST_MOB)
 #if CX_INST_PREC == 0

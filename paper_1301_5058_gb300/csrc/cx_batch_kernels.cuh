@@ -16,9 +16,10 @@ using namespace stencil;
 // One tile (work item w) of one step.
 // stage 0: u_out(parity^1) = u(parity) + dt r(u(parity))
 // stage 1: u(parity) = (u(parity) + u*(parity^1) + dt r(u*)) / 2, in place
-template <typename T, int LAW, int MOB, int STAGE, bool CG>
+// NOISE 1: sigma is redrawn for time step `step` (both Heun stages share it).
+template <typename T, int LAW, int MOB, int NOISE, int STAGE, bool CG>
 __device__ __forceinline__ void tile_step(const InstDev<T> *__restrict__ inst, const int4 w,
-                                          int parity, int rows)
+                                          int parity, int rows, uint64_t step)
 {
     const InstDev<T> &I = inst[w.x];
     const int nx = I.nx, ny = I.ny;
@@ -32,21 +33,21 @@ __device__ __forceinline__ void tile_step(const InstDev<T> *__restrict__ inst, c
         P = Ptrs<T>{I.b[parity ^ 1], I.n[parity ^ 1], I.s, I.b[parity], I.n[parity],
                     I.b[parity], I.n[parity]};
     }
-    NoiseT<T> nz{};
+    const NoiseT<T> nz = NOISE ? inst_noise(I, step) : NoiseT<T>{};
     const int x0 = (w.y * kThreads + threadIdx.x) * kCells;
     const int j0 = w.z * rows;
     const int jend = min(j0 + rows, ny);
     const bool interior = w.y > 0 && (w.y + 1) * kThreads * kCells < nx;
     if (w.z & 1) {
         if (interior)
-            march<T, LAW, MOB, 0, STAGE, -1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+            march<T, LAW, MOB, NOISE, STAGE, -1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
         else
-            march<T, LAW, MOB, 0, STAGE, -1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+            march<T, LAW, MOB, NOISE, STAGE, -1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
     } else {
         if (interior)
-            march<T, LAW, MOB, 0, STAGE, +1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+            march<T, LAW, MOB, NOISE, STAGE, +1, CG, true>(P, nx, ny, pitch, k, nz, x0, j0, jend);
         else
-            march<T, LAW, MOB, 0, STAGE, +1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
+            march<T, LAW, MOB, NOISE, STAGE, +1, CG>(P, nx, ny, pitch, k, nz, x0, j0, jend);
     }
 }
 
@@ -96,19 +97,24 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb, long long spin_lim
 // Heun forms still spill a little at 255 registers.
 template <typename T> constexpr int resident_min_blocks() { return 2; }
 
-template <typename T, int LAW, int MOB, int HEUN>
+// The time step of the first pass of a launch is *step_base + step_off:
+// the host writes step_base before a captured graph is replayed, and the
+// passes inside the graph add their fixed offsets (read only with NOISE 1).
+template <typename T, int LAW, int MOB, int NOISE, int HEUN>
 __global__ void __launch_bounds__(kThreads, resident_min_blocks<T>())
     batch_resident_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                           int nwork, int parity, int rows, int nsteps, GridBarrier *gb,
-                          long long spin_limit)
+                          long long spin_limit, const long long *__restrict__ step_base,
+                          int step_off)
 {
+    const uint64_t step0 = NOISE ? (uint64_t)(__ldg(step_base) + step_off) : 0;
     for (int s = 0; s < nsteps; ++s) {
         for (int w = blockIdx.x; w < nwork; w += gridDim.x)
-            tile_step<T, LAW, MOB, 0, true>(inst, work[w], parity, rows);
+            tile_step<T, LAW, MOB, NOISE, 0, true>(inst, work[w], parity, rows, step0 + s);
         if (!grid_barrier(gb, spin_limit)) return;
         if (HEUN) {
             for (int w = blockIdx.x; w < nwork; w += gridDim.x)
-                tile_step<T, LAW, MOB, 1, true>(inst, work[w], parity, rows);
+                tile_step<T, LAW, MOB, NOISE, 1, true>(inst, work[w], parity, rows, step0 + s);
             if (!grid_barrier(gb, spin_limit)) return;
         } else {
             parity ^= 1;
@@ -125,12 +131,13 @@ template <typename T, int STAGE> constexpr int batch_min_blocks()
     return sizeof(T) == 4 ? (STAGE == 0 ? 8 : 4) : 2;
 }
 
-template <typename T, int LAW, int MOB, int STAGE>
+template <typename T, int LAW, int MOB, int NOISE, int STAGE>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
     batch_step_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
-                      int parity, int rows)
+                      int parity, int rows, const long long *__restrict__ step_base, int step_off)
 {
-    tile_step<T, LAW, MOB, STAGE, false>(inst, work[blockIdx.x], parity, rows);
+    const uint64_t step = NOISE ? (uint64_t)(__ldg(step_base) + step_off) : 0;
+    tile_step<T, LAW, MOB, NOISE, STAGE, false>(inst, work[blockIdx.x], parity, rows, step);
 }
 
 // Two stages per pass (two Euler steps, or one Heun step) of one tile of the
@@ -138,10 +145,10 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
 // budget as the single-grid two-stage pass (128 registers in FP32).
 template <typename T> constexpr int batch_fused_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <typename T, int LAW, int MOB, bool HEUN>
+template <typename T, int LAW, int MOB, int NOISE, bool HEUN>
 __global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
     batch_fused_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
-                       int parity, int rows)
+                       int parity, int rows, const long long *__restrict__ step_base, int step_off)
 {
     const int4 w = work[blockIdx.x];
     const InstDev<T> &I = inst[w.x];
@@ -150,7 +157,11 @@ __global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
     const KV<P2<T>> k = make_kv(I.k);
     const Ptrs<T> P{I.b[parity], I.n[parity], I.s, nullptr, nullptr, I.b[parity ^ 1],
                     I.n[parity ^ 1]};
-    const NoiseT<T> nz{};
+    // NOISE 1: stage one draws sigma for the pass's first step; Euler's
+    // second stage for the next step, Heun's second stage shares the first's
+    const uint64_t step = NOISE ? (uint64_t)(__ldg(step_base) + step_off) : 0;
+    const NoiseT<T> nz1 = NOISE ? inst_noise(I, step) : NoiseT<T>{};
+    const NoiseT<T> nz2 = NOISE && !HEUN ? inst_noise(I, step + 1) : nz1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xb = w.y * kFusedBlockCols;
     // warps share nothing: one whose written columns all lie past the row's
@@ -162,57 +173,78 @@ __global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
     const bool interior = w.y > 0 && xb + kFusedBlockCols + kCells <= nx;
     if (w.z & 1) {
         if (interior)
-            march2<T, LAW, MOB, 0, HEUN, -1, true>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, -1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
         else
-            march2<T, LAW, MOB, 0, HEUN, -1, false>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, -1, false>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
     } else {
         if (interior)
-            march2<T, LAW, MOB, 0, HEUN, +1, true>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, +1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
         else
-            march2<T, LAW, MOB, 0, HEUN, +1, false>(P, nx, ny, pitch, k, nz, nz, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, +1, false>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
     }
+}
+
+template <typename T, int LAW, int MOB, int NOISE>
+cudaError_t launch_step_n(const void *inst, const int4 *work, int nwork, int parity, int rows,
+                          int stage, const long long *step_base, int step_off, cudaStream_t st)
+{
+    const InstDev<T> *ip = (const InstDev<T> *)inst;
+    if (stage == 0)
+        batch_step_kernel<T, LAW, MOB, NOISE, 0><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
+                                                                             step_base, step_off);
+    else
+        batch_step_kernel<T, LAW, MOB, NOISE, 1><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
+                                                                             step_base, step_off);
+    return cudaGetLastError();
 }
 
 template <typename T, int LAW, int MOB>
 cudaError_t launch_step_lm(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                           int stage, cudaStream_t st)
+                           int stage, int noise, const long long *step_base, int step_off,
+                           cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
-    if (stage == 0)
-        batch_step_kernel<T, LAW, MOB, 0><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst, work,
-                                                                      parity, rows);
+    return noise ? launch_step_n<T, LAW, MOB, 1>(inst, work, nwork, parity, rows, stage, step_base, step_off, st)
+                 : launch_step_n<T, LAW, MOB, 0>(inst, work, nwork, parity, rows, stage, step_base, step_off, st);
+}
+
+template <typename T, int LAW, int MOB, int NOISE>
+cudaError_t launch_fused_n(const void *inst, const int4 *work, int nwork, int parity, int rows,
+                           int heun, const long long *step_base, int step_off, cudaStream_t st)
+{
+    const InstDev<T> *ip = (const InstDev<T> *)inst;
+    if (heun)
+        batch_fused_kernel<T, LAW, MOB, NOISE, true><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
+                                                                                 step_base, step_off);
     else
-        batch_step_kernel<T, LAW, MOB, 1><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst, work,
-                                                                      parity, rows);
+        batch_fused_kernel<T, LAW, MOB, NOISE, false><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
+                                                                                  step_base, step_off);
     return cudaGetLastError();
 }
 
 template <typename T, int LAW, int MOB>
 cudaError_t launch_fused_lm(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                           int heun, cudaStream_t st)
+                            int heun, int noise, const long long *step_base, int step_off,
+                            cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
-    if (heun)
-        batch_fused_kernel<T, LAW, MOB, true><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst,
-                                                                          work, parity, rows);
-    else
-        batch_fused_kernel<T, LAW, MOB, false><<<nwork, kThreads, 0, st>>>((const InstDev<T> *)inst,
-                                                                           work, parity, rows);
-    return cudaGetLastError();
+    return noise ? launch_fused_n<T, LAW, MOB, 1>(inst, work, nwork, parity, rows, heun, step_base, step_off, st)
+                 : launch_fused_n<T, LAW, MOB, 0>(inst, work, nwork, parity, rows, heun, step_base, step_off, st);
 }
 
 // Cooperative launch of the resident kernel with as many blocks as can be
 // resident at once (at most one per tile), so every block reaches every
 // barrier.
-template <typename T, int LAW, int MOB, int HEUN>
+template <typename T, int LAW, int MOB, int NOISE, int HEUN>
 cudaError_t launch_resident_h(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                              int nsteps, void *gb, long long spin, cudaStream_t st)
+                              int nsteps, void *gb, long long spin, const long long *step_base,
+                              int step_off, cudaStream_t st)
 {
     if (nwork <= 0 || nsteps <= 0) return cudaSuccess;
-    const void *kern = (const void *)batch_resident_kernel<T, LAW, MOB, HEUN>;
+    const void *kern = (const void *)batch_resident_kernel<T, LAW, MOB, NOISE, HEUN>;
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, batch_resident_kernel<T, LAW, MOB, HEUN>, kThreads, 0);
+        &per_sm, batch_resident_kernel<T, LAW, MOB, NOISE, HEUN>, kThreads, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -222,16 +254,21 @@ cudaError_t launch_resident_h(const void *inst, const int4 *work, int nwork, int
     const InstDev<T> *ip = (const InstDev<T> *)inst;
     GridBarrier *gp = (GridBarrier *)gb;
     void *args[] = {(void *)&ip, (void *)&work, (void *)&nwork, (void *)&parity, (void *)&rows,
-                    (void *)&nsteps, (void *)&gp, (void *)&spin};
+                    (void *)&nsteps, (void *)&gp, (void *)&spin, (void *)&step_base,
+                    (void *)&step_off};
     return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
 template <typename T, int LAW, int MOB>
 cudaError_t launch_resident_lm(const void *inst, const int4 *work, int nwork, int parity, int rows,
-                              int nsteps, int heun, void *gb, long long spin, cudaStream_t st)
+                               int nsteps, int heun, int noise, void *gb, long long spin,
+                               const long long *step_base, int step_off, cudaStream_t st)
 {
-    return heun ? launch_resident_h<T, LAW, MOB, 1>(inst, work, nwork, parity, rows, nsteps, gb, spin, st)
-                : launch_resident_h<T, LAW, MOB, 0>(inst, work, nwork, parity, rows, nsteps, gb, spin, st);
+    if (noise)
+        return heun ? launch_resident_h<T, LAW, MOB, 1, 1>(inst, work, nwork, parity, rows, nsteps, gb, spin, step_base, step_off, st)
+                    : launch_resident_h<T, LAW, MOB, 1, 0>(inst, work, nwork, parity, rows, nsteps, gb, spin, step_base, step_off, st);
+    return heun ? launch_resident_h<T, LAW, MOB, 0, 1>(inst, work, nwork, parity, rows, nsteps, gb, spin, step_base, step_off, st)
+                : launch_resident_h<T, LAW, MOB, 0, 0>(inst, work, nwork, parity, rows, nsteps, gb, spin, step_base, step_off, st);
 }
 
 }  // namespace batch

@@ -61,6 +61,7 @@ cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
     nz1.dist = a.sg.dist;
     nz1.sigma0 = (T)a.sg.sigma0;
     nz1.amp = (T)a.sg.amp;
+    set_noise_keys(nz1);
     NoiseT<T> nz2 = nz1;
     if (!HEUN) nz2.step = (uint64_t)a.step + 1;
     Ptrs<T> P{(const T *)a.b, (const T *)a.n, (const T *)a.s, nullptr, nullptr, (T *)a.bo,

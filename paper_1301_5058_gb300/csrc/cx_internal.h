@@ -107,13 +107,25 @@ double envelope_level(const cx_params &p);
 // tile y, unused).
 size_t inst_dev_bytes(int prec);
 void fill_inst(int prec, void *table, int i, void *b0, void *b1, void *n0, void *n1, void *s,
-               int nx, int ny, long long pitch, const Coef &k, double bth);
+               int nx, int ny, long long pitch, const Coef &k, double bth, uint64_t seed,
+               double sigma0, double amp, int dist);
+// Per-step noise of a batch pass: on = 1 redraws sigma every step; the
+// pass's first time step is *step_base + step_off (step_base: device int64
+// written by launch_set_step before the pass or the graph holding it).
+struct BatchNoise {
+    int on;
+    const long long *step_base;
+    int step_off;
+};
+cudaError_t launch_set_step(long long *step_base, long long step, cudaStream_t st);
 cudaError_t launch_batch_step(int prec, int law, int mob, const void *inst, const int4 *work,
-                              int nwork, int parity, int rows, int stage, cudaStream_t st);
+                              int nwork, int parity, int rows, int stage, const BatchNoise &nz,
+                              cudaStream_t st);
 // Two stages per pass over a 480-column work list: reads u(parity), writes
 // u(parity^1); heun 0: two Euler steps, 1: one Heun step.
 cudaError_t launch_batch_fused(int prec, int law, int mob, const void *inst, const int4 *work,
-                               int nwork, int parity, int rows, int heun, cudaStream_t st);
+                               int nwork, int parity, int rows, int heun, const BatchNoise &nz,
+                               cudaStream_t st);
 cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, int blocks,
                               int parity, double *part, double *out, cudaStream_t st);
 // nsteps steps of the work items [0, nwork) in one cooperative launch with
@@ -123,7 +135,8 @@ cudaError_t launch_batch_diag(int prec, const void *inst, int first, int count, 
 size_t grid_barrier_bytes();
 cudaError_t launch_batch_resident(int prec, int law, int mob, const void *inst, const int4 *work,
                                   int nwork, int parity, int rows, int nsteps, int heun,
-                                  void *barrier, long long spin_limit, cudaStream_t st);
+                                  void *barrier, long long spin_limit, const BatchNoise &nz,
+                                  cudaStream_t st);
 
 }  // namespace cx
 

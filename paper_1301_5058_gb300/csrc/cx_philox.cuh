@@ -71,6 +71,23 @@ __device__ __forceinline__ float sigma_from_word(uint32_t w, int dist, float sig
     return __fmul_rn(sigma0, __fadd_rn(1.0f, __fmul_rn(amp, d)));
 }
 
+// Philox4x32-10 with the key schedule given: round r uses (kx[r], ky[r]) =
+// (k0 + r W0, k1 + r W1) mod 2^32, the keys the rounds above derive one by
+// one.  The schedule is the same for every cell of a launch, so the host
+// computes it once and the rounds read it as operands.
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t (&kx)[10],
+                                                  const uint32_t (&ky)[10])
+{
+    constexpr uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = M0 * (uint64_t)c.x, p1 = M1 * (uint64_t)c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ kx[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ ky[r], (uint32_t)p0);
+    }
+    return c;
+}
+
 // the Philox block of cells 4q .. 4q+3
 __device__ __forceinline__ uint4 sigma_block_f32(uint64_t seed, uint64_t q, uint64_t step)
 {

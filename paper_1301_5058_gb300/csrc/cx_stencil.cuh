@@ -344,9 +344,27 @@ template <> struct NoiseT<float> {
     uint64_t seed, step;
     int dist;
     float sigma0, amp;
+    uint32_t kx[10], ky[10];  // the key schedule of seed (set_keys)
+    __host__ __device__ void set_keys()
+    {
+        uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            kx[r] = a;
+            ky[r] = b;
+            a += 0x9E3779B9u;
+            b += 0xBB67AE85u;
+        }
+    }
+    __device__ __forceinline__ uint4 block(uint64_t q) const
+    {
+        return philox4x32_10_ks(
+            make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)step, (uint32_t)(step >> 32)), kx,
+            ky);
+    }
     __device__ __forceinline__ float at(long long idx) const
     {
-        return sigma_f32(seed, (uint64_t)idx, step, dist, sigma0, amp);
+        const uint4 w = block((uint64_t)idx >> 2);
+        return sigma_from_word(block_word(w, (int)(idx & 3)), dist, sigma0, amp);
     }
     // cells idx0 .. idx0+3: one Philox block when idx0 is a multiple of 4
     // (always, in rows whose width is), two otherwise (the offset is the same
@@ -355,14 +373,14 @@ template <> struct NoiseT<float> {
     {
         const uint64_t q = (uint64_t)idx0 >> 2;
         const int h = (int)(idx0 & 3);
-        const uint4 w0 = sigma_block_f32(seed, q, step);
+        const uint4 w0 = block(q);
         if (h == 0) {
             s[0] = sigma_from_word(w0.x, dist, sigma0, amp);
             s[1] = sigma_from_word(w0.y, dist, sigma0, amp);
             s[2] = sigma_from_word(w0.z, dist, sigma0, amp);
             s[3] = sigma_from_word(w0.w, dist, sigma0, amp);
         } else {
-            const uint4 w1 = sigma_block_f32(seed, q + 1, step);
+            const uint4 w1 = block(q + 1);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int k = h + c;
@@ -386,6 +404,11 @@ template <> struct NoiseT<double> {
         for (int c = 0; c < 4; ++c) s[c] = at(idx0 + c);
     }
 };
+
+// Before a launch: the FP32 recipe's Philox key schedule from the seed (the
+// FP64 recipe derives its keys as it goes).
+inline void set_noise_keys(NoiseT<float> &nz) { nz.set_keys(); }
+inline void set_noise_keys(NoiseT<double> &) {}
 
 template <typename T> struct Ptrs {
     const T *__restrict__ b;

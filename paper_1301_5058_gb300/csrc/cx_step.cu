@@ -73,6 +73,7 @@ cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
     nz.dist = a.sg.dist;
     nz.sigma0 = (T)a.sg.sigma0;
     nz.amp = (T)a.sg.amp;
+    set_noise_keys(nz);
     Ptrs<T> P{(const T *)a.b, (const T *)a.n, (const T *)a.s, (const T *)a.bu,
               (const T *)a.nu, (T *)a.bo, (T *)a.no};
     const dim3 grid((a.nx + kThreads * kCells - 1) / (kThreads * kCells),

@@ -169,10 +169,11 @@ def test_batch_create_validates_before_any_device_call(cx):
     with pytest.raises(cx.CxError) as e:
         cx.cx_batch_create(g, [p32, cx.cx_params_default(noise_amp=2.0)], [0, 1])
     assert e.value.code == cx.CX_ERR_INVALID_ARG
+    # instances must share the noise mode (per-step noise itself is supported)
     ps = cx.cx_params_default(noise_mode=cx.CX_NOISE_PER_STEP)
     with pytest.raises(cx.CxError) as e:
-        cx.cx_batch_create(g, [ps, ps], [0, 1])
-    assert e.value.code == cx.CX_ERR_UNSUPPORTED
+        cx.cx_batch_create(g, [p32, ps], [0, 1])
+    assert e.value.code == cx.CX_ERR_INVALID_ARG
     bad = cx.cx_params_default(dt=10.0)
     with pytest.raises(cx.CxError) as e:
         cx.cx_batch_create(g, [p32, bad], [0, 1])

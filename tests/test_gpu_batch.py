@@ -23,13 +23,17 @@ def cx():
 SIZES = [(64, 48), (130, 70), (513, 33), (7, 5), (600, 97), (1, 1)]
 
 
-def specs(prec, scheme=0, sizes=SIZES):
+def specs(prec, scheme=0, sizes=SIZES, noise=None):
+    """Instances of a sweep; noise=(mode, dist) sets the sigma noise (default
+    static uniform)."""
     n0, chi0, sigma0 = W.sweep_points(len(sizes), seed=4)
     out = []
     for i, (nx, ny) in enumerate(sizes):
         out.append(dict(nx=nx, ny=ny, dx=1.0, seed=100 + i, n0=float(n0[i]), chi0=float(chi0[i]),
                         sigma0=float(sigma0[i]), noise_amp=0.5, bM=0.71, r0sq=16.0,
                         precision=prec, scheme=scheme))
+        if noise is not None:
+            out[-1].update(noise_mode=noise[0], noise_dist=noise[1])
     return out
 
 
@@ -68,6 +72,52 @@ def test_batch_matches_single_grids_bitwise(cx, prec, scheme, tuning):
             assert d[k] == pytest.approx(r[k], rel=1e-13)
         for k in ("min_b", "min_n", "max_b", "r_env", "step", "t", "dt", "finite"):
             assert d[k] == r[k], k
+
+
+# The paper's own scheme in a sweep (Sec. 3): sigma redrawn at every point and
+# step from a triangular law, with forward Euler or Heun.  Each instance draws
+# from (its seed, cell, step) exactly as a single grid does, so it must match
+# that grid bit for bit under every tuning, across two calls (the step index
+# carries over) and through graph replays (the step is read on the device).
+@pytest.mark.parametrize("prec,scheme", [(1, 0), (1, 1), (0, 0), (0, 1)])
+@pytest.mark.parametrize("tuning", [(32, 0, 0, 0), (8, 10, 0, 0), (16, 12, 400_000, 0),
+                                    (4, 0, 0, 50), (32, 0, 0, 0, 1), (8, 10, 0, 0, 1),
+                                    (64, 64, 0, 0, 2), (5, 6, 0, 0, 2)])
+def test_batch_per_step_noise_matches_single_grids_bitwise(cx, prec, scheme, tuning):
+    sp = specs(prec, scheme, noise=(1, 1))
+    dtype = np.float32 if prec == 1 else np.float64
+    steps = 131
+    ref = single_runs(cx, sp, steps, dtype)
+    with cx.Batch(sp) as bt:
+        bt.tune(*tuning)
+        bt.step(60)
+        bt.step(steps - 60)
+        for i in range(len(sp)):
+            assert np.array_equal(bt.field(i, cx.CX_FIELD_B, dtype), ref[i][0]), i
+            assert np.array_equal(bt.field(i, cx.CX_FIELD_N, dtype), ref[i][1]), i
+
+
+@pytest.mark.parametrize("prec,scheme,tol", [(1, 1, 1e-4), (0, 1, 1e-12), (1, 0, 1e-4)])
+def test_batch_per_step_noise_instance_matches_oracle(cx, prec, scheme, tol):
+    # the oracle redraws sigma before every step by the recipe of the state's
+    # precision (FP32 state: the four-cells-per-block FP32 recipe)
+    sp = specs(prec, scheme, sizes=[(90, 70), (33, 40)], noise=(1, 1))
+    steps = 300
+    with cx.Batch(sp) as bt:
+        s = sp[0]
+        b, n = oracle.initial_state(90, 70, 1.0, s["n0"], s["bM"], s["r0sq"])
+        bt.set_field(0, cx.CX_FIELD_B, b)
+        bt.set_field(0, cx.CX_FIELD_N, n)
+        bt.step(steps)
+        gb = bt.field(0, cx.CX_FIELD_B)
+        gn = bt.field(0, cx.CX_FIELD_N)
+        dt = bt.diagnostics()[0]["dt"]
+    ob, on, _ = oracle.run(np.zeros((70, 90)), b, n, steps, dx=1.0, dt=dt, Dn=1.0, theta=1.0,
+                           chi0=s["chi0"], scheme=scheme, noise_mode=1, seed=s["seed"],
+                           sigma0=s["sigma0"], amp=s["noise_amp"], dist=1,
+                           recipe=1 if prec == 1 else 0)
+    assert np.linalg.norm(gb - ob) <= tol * np.linalg.norm(ob)
+    assert np.linalg.norm(gn - on) <= tol * np.linalg.norm(on)
 
 
 def test_batch_instance_matches_oracle(cx):
