@@ -121,6 +121,9 @@ typedef struct {
     double r_env;     /* largest cell-centre distance with b >= b_threshold, 0 if none */
     int32_t finite;   /* 1 if every b and n is finite */
     int32_t status;   /* CX_OK, CX_ERR_NONFINITE or CX_ERR_NEGATIVE */
+    double area_env;  /* dx^2 x the number of cells with b >= b_threshold: the area
+                         of the colony, whose equivalent radius sqrt(area_env / pi)
+                         averages the front over every direction */
 } cx_diag;
 
 /* ---- host-only helpers (no GPU needed) ---------------------------------- */
@@ -234,7 +237,8 @@ int cx_get_time(cx_ctx *c, int64_t *step, double *t, double *dt);
 int cx_set_step(cx_ctx *c, int64_t step);
 
 /* Height in rows of one step-kernel tile (each CTA marches one tile of
- * 512 columns x rows, 480 x rows with two stages per pass), 1..4096 with
+ * 512 columns x rows; with two stages per pass, 120 x rows per one-warp
+ * CTA, or 480 x rows per four-warp CTA when sigma is redrawn every step), 1..4096 with
  * ceil(ny/rows) <= 65535, or 0 for the automatic height; a performance
  * knob that the autotuner sets.  The result is bit-identical for every
  * value.  Automatic: 32 rows (64 with two stages per pass), or fewer on
@@ -313,7 +317,7 @@ int cx_batch_get_tuning(cx_batch *b, int32_t *tile_rows, int32_t *graph_steps, i
 
 /* Temporal blocking depth of the batch, as cx_set_time_block: 2 takes two
  * Euler steps (or one whole Heun step) per pass over every instance, on
- * 480-column tiles; 1 one step per pass.  Results are bit-identical for
+ * 120-column one-warp tiles; 1 one step per pass.  Results are bit-identical for
  * both.  Default: 2 for FP32 batches, 1 for FP64.  The resident mode
  * (resident_steps > 0) takes one stage per pass whatever the depth.
  * Errors: INVALID_ARG. */
@@ -411,7 +415,7 @@ void cx_mlp_destroy(cx_mlp *m);
  *   result_dev  caller-owned device array of 8 doubles that receives
  *               {sum b, sum n, min b, min n, max b, max (2i+1-nx)^2 +
  *               (2j+1-ny)^2 over b >= b_threshold (-1 if none),
- *               non-finite flag, 0};
+ *               non-finite flag, number of cells with b >= b_threshold};
  *   out         optional host struct: if non-NULL the call copies the
  *               record back, waits for `stream` and fills *out (step, t and
  *               dt are 0: there is no handle).  If NULL the call only

@@ -194,7 +194,8 @@ def run(sigma, b, n, nsteps, *, dx, dt, Dn, theta, chi0, chemo_law=0, mobility=0
     return bb, nn, s
 
 
-DIAG_KEYS = ("mass_b", "mass_n", "invariant", "min_b", "min_n", "max_b", "r_env", "finite")
+DIAG_KEYS = ("mass_b", "mass_n", "invariant", "min_b", "min_n", "max_b", "r_env", "finite",
+             "area_env")
 
 
 def omp_threads() -> int:
@@ -205,9 +206,10 @@ def omp_threads() -> int:
 
 def diagnostics(b, n, *, dx, theta, b_th) -> dict:
     """Masses, the conserved invariant dx^2 sum(b + theta n), extrema, the
-    envelope radius and a finiteness flag."""
+    envelope radius, a finiteness flag and the colony's area (cells with
+    b >= b_th times dx^2)."""
     ny, nx = b.shape
-    out = np.zeros(8, np.float64)
+    out = np.zeros(9, np.float64)
     rc = _load().orc_diagnostics(nx, ny, dx, theta, b_th,
                                  _ptr(np.ascontiguousarray(b, np.float64)),
                                  _ptr(np.ascontiguousarray(n, np.float64)), _ptr(out))

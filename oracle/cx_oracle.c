@@ -357,9 +357,11 @@ static double pairwise_sum(const double *x, size_t len)
  *        telescope)
  * out[3] min b, out[4] min n, out[5] max b
  * out[6] r_env = largest centre distance of a cell with b >= b_th (0 if none)
- * out[7] 1 if every b and n is finite, else 0 */
+ * out[7] 1 if every b and n is finite, else 0
+ * out[8] area_env = dx^2 x the number of cells with b >= b_th (the colony's
+ *        area; sqrt(area_env / pi) is its equivalent radius) */
 int orc_diagnostics(int nx, int ny, double dx, double theta, double b_th,
-                    const double *b, const double *n, double out[8])
+                    const double *b, const double *n, double out[9])
 {
     size_t N = (size_t)nx * (size_t)ny;
     double *tmp = (double *)malloc(N * sizeof(double));
@@ -371,6 +373,7 @@ int orc_diagnostics(int nx, int ny, double dx, double theta, double b_th,
     out[2] = area * pairwise_sum(tmp, N);
     free(tmp);
     double mnb = b[0], mnn = n[0], mxb = b[0], r2max = -1.0;
+    long long above = 0;
     int finite = 1;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -380,6 +383,7 @@ int orc_diagnostics(int nx, int ny, double dx, double theta, double b_th,
             if (n[p] < mnn) mnn = n[p];
             if (b[p] > mxb) mxb = b[p];
             if (b[p] >= b_th) {
+                ++above;
                 double x = ((double)i + 0.5 - 0.5 * (double)nx) * dx;
                 double y = ((double)j + 0.5 - 0.5 * (double)ny) * dx;
                 double r2 = x * x + y * y;
@@ -389,6 +393,7 @@ int orc_diagnostics(int nx, int ny, double dx, double theta, double b_th,
     out[3] = mnb; out[4] = mnn; out[5] = mxb;
     out[6] = r2max >= 0.0 ? sqrt(r2max) : 0.0;
     out[7] = finite ? 1.0 : 0.0;
+    out[8] = area * (double)above;
     return 0;
 }
 

@@ -55,7 +55,8 @@ class cx_diag(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64)] + \
                [(k, ctypes.c_double) for k in
                 ("t", "dt", "mass_b", "mass_n", "invariant", "min_b", "min_n", "max_b", "r_env")] + \
-               [("finite", ctypes.c_int32), ("status", ctypes.c_int32)]
+               [("finite", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("area_env", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -502,6 +502,7 @@ int cx_diagnostics(cx_ctx *c, cx_diag *out)
     out->min_n = h[3];
     out->max_b = h[4];
     out->r_env = h[5] >= 0.0 ? 0.5 * c->g.dx * sqrt(h[5]) : 0.0;
+    out->area_env = c->g.dx * c->g.dx * h[7];
     out->finite = h[6] == 0.0 ? 1 : 0;
     out->status = CX_OK;
     if (!out->finite)

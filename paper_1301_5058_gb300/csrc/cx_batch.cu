@@ -13,7 +13,8 @@
 // each group runs all its steps before the next starts.
 //
 // With two stages per pass (batch_fused_kernel) a second work list holds
-// one entry per 480-column x `rows`-row tile of the two-stage march.
+// one entry per 120-column x `rows`-row tile (one warp) of the two-stage
+// march.
 //
 // Every instance goes through the same per-thread stencil code as a single
 // grid (cx_stencil.cuh, cx_fused.cuh), so a batch instance and a cx_ctx with

@@ -28,7 +28,7 @@ int bcuda(cudaError_t e, const char *what)
     } while (0)
 
 constexpr int kTileCols = 512;       // columns per tile (128 threads x 4 cells)
-constexpr int kFusedTileCols = 480;  // written columns per tile of the two-stage march
+constexpr int kFusedTileCols = 120;  // written columns per (one-warp) tile of the two-stage march
 constexpr int kDiagBlocksPerInst = 64;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -52,7 +52,7 @@ struct cx_batch {
     std::vector<unsigned char> h_inst;
     int4 *d_work = nullptr;       // 512-column tiles (one stage per pass)
     std::vector<int> work_begin;  // first work item of each instance (+ total)
-    int4 *d_work2 = nullptr;      // 480-column tiles (two stages per pass)
+    int4 *d_work2 = nullptr;      // 120-column tiles (two stages per pass)
     std::vector<int> work2_begin;
     int rows = 32;
     int graph_steps = 64;
@@ -102,7 +102,7 @@ void free_batch(cx_batch *B)
 }
 
 // Tile work lists for the current tile height, instance by instance: the
-// one-stage march's 512-column tiles and the two-stage march's 480-column
+// one-stage march's 512-column tiles and the two-stage march's 120-column
 // tiles.
 int build_work(cx_batch *B)
 {
@@ -541,6 +541,7 @@ int cx_batch_diagnostics(cx_batch *B, cx_diag *out)
         d.min_n = h[3];
         d.max_b = h[4];
         d.r_env = h[5] >= 0.0 ? 0.5 * B->g[i].dx * sqrt(h[5]) : 0.0;
+        d.area_env = area * h[7];
         d.finite = h[6] == 0.0 ? 1 : 0;
         d.status = !d.finite ? CX_ERR_NONFINITE
                              : ((d.min_b < 0.0 || d.min_n < 0.0) ? CX_ERR_NEGATIVE : CX_OK);

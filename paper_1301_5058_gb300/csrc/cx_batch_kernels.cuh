@@ -141,12 +141,15 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<T, STAGE>())
 }
 
 // Two stages per pass (two Euler steps, or one Heun step) of one tile of the
-// 480-column work list: reads u(parity), writes u(parity^1).  Register
-// budget as the single-grid two-stage pass (128 registers in FP32).
-template <typename T> constexpr int batch_fused_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
+// 120-column work list, one warp per block: reads u(parity), writes
+// u(parity^1).  One-warp blocks fit the sweep's 512..2048-wide instances,
+// which four-warp (480-column) tiles cover with partly idle blocks.
+// Register budget as the single-grid two-stage pass (128 registers in FP32).
+constexpr int kBatchFusedThreads = 32;
+template <typename T> constexpr int batch_fused_min_blocks() { return sizeof(T) == 4 ? 16 : 8; }
 
 template <typename T, int LAW, int MOB, int NOISE, bool HEUN>
-__global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
+__global__ void __launch_bounds__(kBatchFusedThreads, batch_fused_min_blocks<T>())
     batch_fused_kernel(const InstDev<T> *__restrict__ inst, const int4 *__restrict__ work,
                        int parity, int rows, const long long *__restrict__ step_base, int step_off)
 {
@@ -162,15 +165,13 @@ __global__ void __launch_bounds__(kThreads, batch_fused_min_blocks<T>())
     const uint64_t step = NOISE ? (uint64_t)(__ldg(step_base) + step_off) : 0;
     const NoiseT<T> nz1 = NOISE ? inst_noise(I, step) : NoiseT<T>{};
     const NoiseT<T> nz2 = NOISE && !HEUN ? inst_noise(I, step + 1) : nz1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int xb = w.y * kFusedBlockCols;
-    // warps share nothing: one whose written columns all lie past the row's
-    // end (ragged last tile) leaves at once
-    if (xb + warp * kFusedCols >= nx) return;
-    const int x0 = xb + warp * kFusedCols - kCells + lane * kCells;
+    const int lane = threadIdx.x & 31;
+    const int xb = w.y * kFusedCols;  // first written column of the tile
+    const int x0 = xb - kCells + lane * kCells;
     const int j0 = w.z * rows;
     const int jend = min(j0 + rows, ny);
-    const bool interior = w.y > 0 && xb + kFusedBlockCols + kCells <= nx;
+    // every column the warp holds, xb - 4 .. xb + 123, lies inside the grid
+    const bool interior = w.y > 0 && xb + kFusedCols + kCells <= nx;
     if (w.z & 1) {
         if (interior)
             march2<T, LAW, MOB, NOISE, HEUN, -1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
@@ -214,11 +215,11 @@ cudaError_t launch_fused_n(const void *inst, const int4 *work, int nwork, int pa
 {
     const InstDev<T> *ip = (const InstDev<T> *)inst;
     if (heun)
-        batch_fused_kernel<T, LAW, MOB, NOISE, true><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
-                                                                                 step_base, step_off);
+        batch_fused_kernel<T, LAW, MOB, NOISE, true><<<nwork, kBatchFusedThreads, 0, st>>>(
+            ip, work, parity, rows, step_base, step_off);
     else
-        batch_fused_kernel<T, LAW, MOB, NOISE, false><<<nwork, kThreads, 0, st>>>(ip, work, parity, rows,
-                                                                                  step_base, step_off);
+        batch_fused_kernel<T, LAW, MOB, NOISE, false><<<nwork, kBatchFusedThreads, 0, st>>>(
+            ip, work, parity, rows, step_base, step_off);
     return cudaGetLastError();
 }
 

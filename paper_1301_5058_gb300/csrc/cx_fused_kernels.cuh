@@ -24,20 +24,22 @@ template <typename T> constexpr int fused_min_blocks()
 }
 
 template <typename T, int LAW, int MOB, int NOISE, bool HEUN>
-__global__ void __launch_bounds__(kThreads, fused_min_blocks<T>())
+__global__ void __launch_bounds__(fused_threads<NOISE>(),
+                                  fused_min_blocks<T>() * (kThreads / fused_threads<NOISE>()))
     fused_kernel(Ptrs<T> P, int nx, int ny, long long pitch, KV<P2<T>> k, NoiseT<T> nz1,
                  NoiseT<T> nz2, int rows)
 {
+    constexpr int kBlockCols = (fused_threads<NOISE>() / 32) * kFusedCols;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int xb = blockIdx.x * kFusedBlockCols;  // first written column of the block
+    const int xb = blockIdx.x * kBlockCols;  // first written column of the block
     // warps share nothing, so a warp whose written columns all lie past the
     // row's end (ragged last tile) leaves at once
     if (xb + warp * kFusedCols >= nx) return;
     const int x0 = xb + warp * kFusedCols - kCells + lane * kCells;
     const int j0 = blockIdx.y * rows;
     const int jend = min(j0 + rows, ny);
-    // every column the block holds, xb - 4 .. xb + 483, lies inside the grid
-    const bool interior = blockIdx.x > 0 && xb + kFusedBlockCols + kCells <= nx;
+    // every column the block holds, xb - 4 .. xb + kBlockCols + 3, lies inside the grid
+    const bool interior = blockIdx.x > 0 && xb + kBlockCols + kCells <= nx;
     if (blockIdx.y & 1) {
         if (interior)
             march2<T, LAW, MOB, NOISE, HEUN, -1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
@@ -66,8 +68,10 @@ cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
     if (!HEUN) nz2.step = (uint64_t)a.step + 1;
     Ptrs<T> P{(const T *)a.b, (const T *)a.n, (const T *)a.s, nullptr, nullptr, (T *)a.bo,
               (T *)a.no};
-    const dim3 grid((a.nx + kFusedBlockCols - 1) / kFusedBlockCols, (a.ny + a.rows - 1) / a.rows);
-    fused_kernel<T, LAW, MOB, NOISE, HEUN><<<grid, kThreads, 0, st>>>(P, a.nx, a.ny, a.pitch, k,
+    constexpr int threads = fused_threads<NOISE>();
+    constexpr int cols = (threads / 32) * kFusedCols;
+    const dim3 grid((a.nx + cols - 1) / cols, (a.ny + a.rows - 1) / a.rows);
+    fused_kernel<T, LAW, MOB, NOISE, HEUN><<<grid, threads, 0, st>>>(P, a.nx, a.ny, a.pitch, k,
                                                                       nz1, nz2, a.rows);
     return cudaGetLastError();
 }

@@ -153,6 +153,7 @@ extern "C" int cx_diagnostics_noalloc(const void *b, const void *n, int32_t nx, 
     out->min_n = h[3];
     out->max_b = h[4];
     out->r_env = h[5] >= 0.0 ? 0.5 * dx * sqrt(h[5]) : 0.0;
+    out->area_env = dx * dx * h[7];
     out->finite = h[6] == 0.0 ? 1 : 0;
     out->status = !out->finite ? CX_ERR_NONFINITE
                                : ((out->min_b < 0.0 || out->min_n < 0.0) ? CX_ERR_NEGATIVE : CX_OK);

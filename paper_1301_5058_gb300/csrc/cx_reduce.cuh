@@ -1,7 +1,8 @@
 // cx_reduce.cuh -- the diagnostics reduction shared by the single-grid and
 // batched diagnostics kernels: one record per thread / warp / block with
 // the sums of b and n, min b, min n, max b, the largest
-// (2i+1-nx)^2 + (2j+1-ny)^2 over cells with b >= b_th, and a non-finite flag.
+// (2i+1-nx)^2 + (2j+1-ny)^2 over cells with b >= b_th, a non-finite flag and
+// the number of cells with b >= b_th.
 #pragma once
 
 #include <float.h>
@@ -19,6 +20,7 @@ struct Acc {
     double mnb, mnn, mxb;
     long long r2;   // max (2i+1-nx)^2 + (2j+1-ny)^2 over b >= threshold, -1 if none
     int bad;        // 1 if a non-finite cell was seen
+    long long cnt;  // cells with b >= threshold
 };
 
 __device__ __forceinline__ void combine(Acc &a, const Acc &o)
@@ -30,6 +32,7 @@ __device__ __forceinline__ void combine(Acc &a, const Acc &o)
     a.mxb = fmax(a.mxb, o.mxb);
     a.r2 = max(a.r2, o.r2);
     a.bad |= o.bad;
+    a.cnt += o.cnt;
 }
 
 __device__ __forceinline__ Acc shfl_down(const Acc &a, int d)
@@ -42,6 +45,7 @@ __device__ __forceinline__ Acc shfl_down(const Acc &a, int d)
     o.mxb = __shfl_down_sync(0xffffffffu, a.mxb, d);
     o.r2 = __shfl_down_sync(0xffffffffu, a.r2, d);
     o.bad = __shfl_down_sync(0xffffffffu, a.bad, d);
+    o.cnt = __shfl_down_sync(0xffffffffu, a.cnt, d);
     return o;
 }
 
@@ -50,7 +54,7 @@ __device__ __forceinline__ Acc empty_acc()
     Acc a;
     a.sb = 0.0; a.sn = 0.0;
     a.mnb = DBL_MAX; a.mnn = DBL_MAX; a.mxb = -DBL_MAX;
-    a.r2 = -1; a.bad = 0;
+    a.r2 = -1; a.bad = 0; a.cnt = 0;
     return a;
 }
 
@@ -78,7 +82,7 @@ __device__ __forceinline__ void store_acc(double *dst, const Acc &a)
     // 2^-53 (no overflow: |2i+1-nx| < 2^31)
     dst[5] = (double)a.r2;
     dst[6] = (double)a.bad;
-    dst[7] = 0.0;
+    dst[7] = (double)a.cnt;  // exact: at most 2^32 cells
 }
 
 __device__ __forceinline__ Acc load_acc(const double *p)
@@ -87,6 +91,7 @@ __device__ __forceinline__ Acc load_acc(const double *p)
     o.sb = p[0]; o.sn = p[1]; o.mnb = p[2]; o.mnn = p[3]; o.mxb = p[4];
     o.r2 = (long long)p[5];
     o.bad = (int)p[6];
+    o.cnt = (long long)p[7];
     return o;
 }
 
@@ -111,6 +116,7 @@ __device__ __forceinline__ Acc rows_f64(const double *__restrict__ b, const doub
             if (vb >= bth) {
                 const long long ddx = 2LL * i + 1 - nx;
                 a.r2 = max(a.r2, ddx * ddx + dy * dy);
+                ++a.cnt;
             }
         }
     }
@@ -142,13 +148,13 @@ __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float
 {
     double sb = 0.0, sn = 0.0;
     float mnb = FLT_MAX, mnn = FLT_MAX, mxb = -FLT_MAX;
-    long long r2 = -1;
+    long long r2 = -1, cnt = 0;
     int bad = 0;
     for (int j = j0; j < ny; j += jstep) {
         const float *rb = b + (long long)j * pitch;
         const float *rn = n + (long long)j * pitch;
         float bs = 0.f, bc = 0.f, ns = 0.f, nc = 0.f;
-        int imin = 0x7fffffff, imax = -1;
+        int imin = 0x7fffffff, imax = -1, above = 0;
         auto cell = [&](int i, float vb, float vn) {
             two_sum(bs, bc, vb);
             two_sum(ns, nc, vn);
@@ -159,6 +165,7 @@ __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float
             if (vb >= fth) {
                 imin = min(imin, i);
                 imax = max(imax, i);
+                ++above;
             }
         };
         int tail = 0;
@@ -175,6 +182,7 @@ __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float
             tail = nv << 2;
         }
         for (int i = tail + threadIdx.x; i < nx; i += kThreads) cell(i, rb[i], rn[i]);
+        cnt += above;
         sb += (double)bs + (double)bc;
         sn += (double)ns + (double)nc;
         if (imax >= 0) {
@@ -186,7 +194,7 @@ __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float
     Acc a;
     a.sb = sb; a.sn = sn;
     a.mnb = (double)mnb; a.mnn = (double)mnn; a.mxb = (double)mxb;
-    a.r2 = r2; a.bad = bad;
+    a.r2 = r2; a.bad = bad; a.cnt = cnt;
     return a;
 }
 

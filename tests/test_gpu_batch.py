@@ -70,7 +70,7 @@ def test_batch_matches_single_grids_bitwise(cx, prec, scheme, tuning):
     for d, (_, _, r) in zip(diags, ref):
         for k in ("mass_b", "mass_n", "invariant"):
             assert d[k] == pytest.approx(r[k], rel=1e-13)
-        for k in ("min_b", "min_n", "max_b", "r_env", "step", "t", "dt", "finite"):
+        for k in ("min_b", "min_n", "max_b", "r_env", "area_env", "step", "t", "dt", "finite"):
             assert d[k] == r[k], k
 
 

@@ -195,6 +195,7 @@ def test_diagnostics_match_oracle_on_the_same_state(cx, prec):
     for k in ("min_b", "min_n", "max_b"):
         assert d[k] == od[k]
     assert d["r_env"] == pytest.approx(od["r_env"], rel=1e-14)
+    assert d["area_env"] == od["area_env"] and d["area_env"] > 0
     assert d["finite"] == 1 and d["step"] == 400
 
 

@@ -107,6 +107,10 @@ def test_envelope_radius_of_gaussian():
     r2 = x[None, :] ** 2 + y[:, None] ** 2
     inside = r2 <= r0sq * math.log(bM / bth) * (1 + 1e-12)
     assert d["r_env"] == pytest.approx(math.sqrt(r2[inside].max()), rel=1e-14)
+    # the colony's area: the cells of that disc, dx^2 each (enumerated), which
+    # approaches the disc's area pi r0sq ln(bM/b_th) as the cells shrink
+    assert d["area_env"] == inside.sum() * dx * dx
+    assert d["area_env"] == pytest.approx(math.pi * r0sq * math.log(bM / bth), rel=0.02)
 
 
 def test_diagnostics_flags_nonfinite():

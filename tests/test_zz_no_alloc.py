@@ -42,6 +42,7 @@ def _compare(d, ref):
     for k in ("min_b", "min_n", "max_b", "finite", "status"):
         assert d[k] == ref[k], k
     assert d["r_env"] == pytest.approx(ref["r_env"], rel=1e-14)
+    assert d["area_env"] == ref["area_env"]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
