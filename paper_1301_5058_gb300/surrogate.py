@@ -67,35 +67,84 @@ def lsq_slope(t, r) -> float:
     return float(((t - tm) * (r - rm)).sum() / den) if den > 0 else float("nan")
 
 
+def smooth_dt(points, bM=0.71, cfl=0.2, Dn=1.0, theta=1.0, dx=1.0):
+    """A time step for sweep points that is a smooth function of (n0, chi0,
+    sigma0, a) and never above the library's explicit limit: with
+    B = bM + theta n0 and Dc = sigma0 (1 + a) n0 B (1 + chi0 B), the limit
+    min(dx^2 / (4 max(Dn, Dc)), 1 / (4 Dn / dx^2 + B)) is at least
+    1 / (4 (Dn + Dc) / dx^2 + 4 Dn / dx^2 + B), which has no kinks.  Runs of a
+    fixed number of steps then end at a time that varies smoothly with the
+    parameters, and so do their labels."""
+    p = np.asarray(points, np.float64)
+    n0, chi0, s0, a = p[:, 0], p[:, 1], p[:, 2], p[:, 3]
+    B = bM + theta * n0
+    Dc = s0 * (1.0 + a) * n0 * B * (1.0 + chi0 * B)
+    return cfl / (4.0 * (Dn + Dc) / dx ** 2 + 4.0 * Dn / dx ** 2 + B)
+
+
 def solver_labels(points, side=256, steps=4000, samples=40, seed0=0, r0sq=64.0,
-                  nsamples=4096, tune=None):
+                  nsamples=4096, tune=None, label="max", sides=None, chunk=2048, info=None,
+                  dt=None):
     """Run every point as one batch instance and return (velocity, branches)
-    arrays plus the per-instance diagnostics at the end."""
+    arrays plus the per-instance diagnostics at the end.
+
+    label "max": the velocity is the slope of r_env, the largest distance of
+    a cell above the envelope level; "area": the slope of the colony's
+    equivalent radius sqrt(area_env / pi), which averages the front over
+    every direction (its seed-to-seed spread is several times smaller).
+    sides: per-point grid sides (default `side` for all); the points are run
+    in batches of at most `chunk` instances.  dt: per-point time steps
+    (default: the library's, 0.2 x the stability limit).  info: a dict that
+    receives the per-point end time, final radii, sides and histories."""
     pts = np.asarray(points, np.float64)
-    specs = [dict(nx=side, ny=side, dx=1.0, seed=seed0 + i, n0=float(p[0]), chi0=float(p[1]),
-                  sigma0=float(p[2]), noise_amp=float(p[3]), bM=0.71, r0sq=r0sq,
-                  precision=cx.CX_PREC_F32) for i, p in enumerate(pts)]
+    sides = np.full(len(pts), side, int) if sides is None else np.asarray(sides, int)
     every = max(1, steps // samples)
-    t_hist, r_hist = [], []
-    with cx.Batch(specs) as bt:
-        if tune is not None:
-            bt.tune(*tune)
-        for _ in range(samples):
-            bt.step(every)
-            d = bt.diagnostics(check=False)
-            t_hist.append([x["t"] for x in d])
-            r_hist.append([x["r_env"] for x in d])
-        last = d
-        branches = []
-        for i, x in enumerate(last):
-            lvl = 0.1 * specs[i]["n0"]   # the envelope level 0.1 theta n0 (theta = 1)
-            prof = cx.cx_batch_polar_profile(bt.h, i, 0.8 * x["r_env"], nsamples)
-            branches.append(count_runs(prof, lvl))
-    t_hist = np.asarray(t_hist)
-    r_hist = np.asarray(r_hist)
-    half = samples // 2
-    vel = np.array([lsq_slope(t_hist[half:, i], r_hist[half:, i]) for i in range(len(pts))])
-    return vel, np.asarray(branches, np.float64), last
+    vel = np.empty(len(pts))
+    branches = np.empty(len(pts))
+    last = [None] * len(pts)
+    t_end, r_end, ra_end = (np.empty(len(pts)) for _ in range(3))
+    hist_t, hist_r, hist_a = (np.empty((samples, len(pts))) for _ in range(3))
+    for c0 in range(0, len(pts), chunk):
+        idx = range(c0, min(len(pts), c0 + chunk))
+        specs = [dict(nx=int(sides[i]), ny=int(sides[i]), dx=1.0, seed=seed0 + i,
+                      n0=float(pts[i, 0]), chi0=float(pts[i, 1]), sigma0=float(pts[i, 2]),
+                      noise_amp=float(pts[i, 3]), bM=0.71, r0sq=r0sq,
+                      precision=cx.CX_PREC_F32) for i in idx]
+        if dt is not None:
+            for k, i in enumerate(idx):
+                specs[k]["dt"] = float(dt[i])
+        t_hist, r_hist = [], []
+        with cx.Batch(specs) as bt:
+            if tune is not None:
+                bt.tune(*tune)
+            for _ in range(samples):
+                bt.step(every)
+                d = bt.diagnostics(check=False)
+                t_hist.append([x["t"] for x in d])
+                ra = [math.sqrt(x["area_env"] / math.pi) for x in d]
+                rm = [x["r_env"] for x in d]
+                r_hist.append(ra if label == "area" else rm)
+                q = len(t_hist) - 1
+                hist_t[q, idx.start:idx.stop] = t_hist[-1]
+                hist_r[q, idx.start:idx.stop] = rm
+                hist_a[q, idx.start:idx.stop] = ra
+            for k, i in enumerate(idx):
+                x = d[k]
+                last[i] = x
+                lvl = 0.1 * specs[k]["n0"]   # the envelope level 0.1 theta n0 (theta = 1)
+                prof = cx.cx_batch_polar_profile(bt.h, k, 0.8 * x["r_env"], nsamples)
+                branches[i] = count_runs(prof, lvl)
+                t_end[i], r_end[i] = x["t"], x["r_env"]
+                ra_end[i] = math.sqrt(x["area_env"] / math.pi)
+        t_hist = np.asarray(t_hist)
+        r_hist = np.asarray(r_hist)
+        half = samples // 2
+        for k, i in enumerate(idx):
+            vel[i] = lsq_slope(t_hist[half:, k], r_hist[half:, k])
+    if info is not None:
+        info.update(t_end=t_end, r_end=r_end, r_area_end=ra_end, sides=sides, hist_t=hist_t,
+                    hist_r=hist_r, hist_area_r=hist_a, branches=branches)
+    return vel, branches, last
 
 
 def init_params(seed: int) -> np.ndarray:
@@ -121,10 +170,13 @@ class Surrogate:
         self.mean = np.zeros(2)
         self.scale = np.ones(2)
 
-    def fit(self, points, labels, steps=3000, lr=1e-3, batch=256, reinit=True, decay=0):
+    def fit(self, points, labels, steps=3000, lr=1e-3, batch=256, reinit=True, decay=0,
+            schedule="halve"):
         """Adam on the standardised labels.  decay > 0: the steps are split
-        into decay + 1 equal chunks, the rate halved and the rows reshuffled
-        from one chunk to the next (the optimiser state carries over)."""
+        into decay + 1 equal chunks and the rows reshuffled from one chunk to
+        the next (the optimiser state carries over); the rate is halved from
+        chunk to chunk (schedule "halve") or follows a cosine from lr down to
+        lr / (2 (decay + 1)) ("cosine")."""
         X = encode(points)
         Y = np.asarray(labels, np.float64)
         self.mean = Y.mean(0)
@@ -140,7 +192,9 @@ class Surrogate:
             perm = rng.permutation(len(X))
             n = chunk if k < decay else steps - chunk * decay
             if n > 0:
-                losses.append(self.net.train(X[perm], T[perm], batch, n, lr * 0.5 ** k))
+                rate = lr * 0.5 ** k if schedule == "halve" else \
+                    lr * 0.5 * (1.0 + math.cos(math.pi * (k + 0.5) / (decay + 1)))
+                losses.append(self.net.train(X[perm], T[perm], batch, n, rate))
         return np.concatenate(losses)
 
     def predict(self, points) -> np.ndarray:
@@ -348,6 +402,164 @@ def validated_throughput(side=256, steps=20000, n_train=4096, n_test=1024, membe
     return out
 
 
+def initial_area_radius(n0, r0sq, bM=0.71, theta=1.0):
+    """Equivalent radius of the inoculum's part above the envelope level:
+    bM exp(-r^2 / r0sq) >= 0.1 theta n0 inside r^2 <= r0sq ln(bM / (0.1 theta n0))."""
+    q = np.log(bM / (0.1 * theta * np.asarray(n0, np.float64)))
+    return np.sqrt(r0sq * np.maximum(q, 0.0))
+
+
+def end_times(points, steps, bM=0.71, r0sq=32.0 ** 2):
+    """Physical time reached after `steps` steps at each point's time step
+    (the library's default: 0.2 x the stability limit)."""
+    out = np.empty(len(points))
+    g = cx.cx_grid(8, 8, 1.0)
+    for i, p in enumerate(np.asarray(points, np.float64)):
+        prm = cx.cx_params_default(n0=float(p[0]), chi0=float(p[1]), sigma0=float(p[2]),
+                                   noise_amp=float(p[3]), bM=bM, r0sq=r0sq)
+        out[i] = steps * prm.cfl_frac * cx.cx_dt_limit(g, prm)
+    return out
+
+
+def single_instance_seconds(side, steps, point, r0sq=32.0 ** 2, samples=40, repeats=2, dt=0.0):
+    """Wall time of one point stepped alone through cx_step, the plain way:
+    creation, `steps` steps, diagnostics `samples` times, a polar profile."""
+    import time
+    import torch
+    p = point
+    kw = dict(n0=float(p[0]), chi0=float(p[1]), sigma0=float(p[2]), noise_amp=float(p[3]),
+              bM=0.71, r0sq=r0sq, precision=cx.CX_PREC_F32, dt=float(dt))
+    best = float("inf")
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with cx.Sim(side, side, 1.0, seed=0, **kw) as sim:
+            for _ in range(samples):
+                sim.step(steps // samples)
+                d = sim.diagnostics(check=False)
+            cx.cx_polar_profile(sim.h, 0.8 * d["r_env"], 4096)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def validated_sweep(train_side=1024, sides=(512, 1024, 1536, 2048), steps=20000, n_train=8192,
+                    n_test=1024, members=8, train_steps=60000, decay=19, lr=2e-3, seed=0,
+                    bar=0.01, quantile=0.95, wall_frac=0.6, campaign=4, chunk=2048,
+                    r0sq=32.0 ** 2, samples=40, verbose=True, save=None, schedule="cosine"):
+    """Validated sweep points per hour on a mix of grid sizes, with and
+    without the learned screen.
+
+    Training data: n_train solver runs at train_side^2 (the sweep's solver,
+    one batch per `chunk` instances), labelled with the area-radius
+    velocity.  Held-out: n_test points with sides drawn uniformly from
+    `sides`, each run by the solver at its own size and seed.  The screen
+    accepts a point without a solver run when (a) the ensemble's members
+    agree to a relative spread s* and (b) the colony, grown at the predicted
+    velocity from the inoculum, stays within wall_frac of the grid's
+    half-width (the labels are free-space velocities).  s* is the largest
+    spread at which the accepted points of the calibration half of the
+    held-out set meet `bar` at `quantile`; the other half reports the error.
+    Rejected points go to the batched solver, whose every label is exact by
+    construction (a batch instance equals its single grid bit for bit)."""
+    import json
+    import time
+    rng = np.random.default_rng(seed + 5)
+    # training data
+    ptr = draw_points(n_train, seed, a_range=(0.0, 1.0))
+    t0 = time.perf_counter()
+    info_tr = {}
+    vtr, btr, _ = solver_labels(ptr, side=train_side, steps=steps, samples=samples, r0sq=r0sq,
+                                label="area", chunk=chunk, info=info_tr, dt=smooth_dt(ptr))
+    train_data_s = time.perf_counter() - t0
+    # held-out points on the size mix
+    pte = draw_points(n_test, seed + 99, a_range=(0.0, 1.0))
+    ste = rng.choice(np.asarray(sides), size=n_test)
+    info = {}
+    t1 = time.perf_counter()
+    vte, bte, _ = solver_labels(pte, steps=steps, samples=samples, r0sq=r0sq, label="area",
+                                sides=ste, seed0=1_000_000, chunk=chunk, info=info,
+                                dt=smooth_dt(pte))
+    batch_s = (time.perf_counter() - t1) / n_test
+    # the plain way, one point per size class
+    first = {int(sd): int(np.argmax(ste == sd)) for sd in sides}
+    single = {sd: single_instance_seconds(sd, steps, pte[i], r0sq=r0sq, samples=samples,
+                                          dt=smooth_dt(pte[i:i + 1])[0]) for sd, i in first.items()}
+    single_s = float(np.mean([single[int(sd)] for sd in ste]))
+    # the ensemble
+    ok = vtr > 0
+    ens = Ensemble(members, seed, max_batch=8192)
+    t2 = time.perf_counter()
+    ens.fit(ptr[ok], vtr[ok], steps=train_steps, lr=lr, batch=256, decay=decay,
+            schedule=schedule)
+    train_s = time.perf_counter() - t2
+    pool = draw_points(65536, seed + 4242, a_range=(0.0, 1.0))
+    t3 = time.perf_counter()
+    ens.predict(pool)
+    steps * smooth_dt(pool)
+    screen_s = (time.perf_counter() - t3) / len(pool)
+    mean, spread = ens.predict(pte)
+    ens.close()
+    if save:
+        np.savez_compressed(save, ptr=ptr, vtr=vtr, pte=pte, ste=ste, vte=vte, mean=mean,
+                            spread=spread, **{"tr_" + k: v for k, v in info_tr.items()},
+                            **{"te_" + k: v for k, v in info.items()})
+    t_end = steps * smooth_dt(pte)
+    r_pred = initial_area_radius(pte[:, 0], r0sq) + np.maximum(mean, 0.0) * t_end
+    wall_ok = r_pred <= wall_frac * 0.5 * ste
+    rel = np.abs(mean - vte) / np.maximum(np.abs(vte), 1e-12)
+    half = n_test // 2
+    cal, ev = np.arange(half), np.arange(half, n_test)
+    chosen = None
+    grid_s = np.geomspace(1e-4, 0.2, 60)
+    for sv in grid_s:
+        m = (spread[cal] <= sv) & wall_ok[cal]
+        if m.sum() >= 20 and np.quantile(rel[cal][m], quantile) <= bar:
+            chosen = float(sv)
+    out = {"train_side": train_side, "sides": list(map(int, sides)), "steps_per_point": steps,
+           "n_train": n_train, "n_test": n_test, "members": members, "train_steps": train_steps,
+           "label": "slope of sqrt(area_env / pi) over the second half of the run",
+           "time_step": "0.2 / (4 (Dn + Dc) / dx^2 + 4 Dn / dx^2 + B), smooth in the parameters",
+           "training_schedule": f"Adam, {train_steps} steps in {decay + 1} chunks, {schedule} rate from {lr}",
+           "bar": bar, "quantile": quantile, "wall_frac": wall_frac,
+           "heldout_error_all": {"median": float(np.median(rel)),
+                                 "p90": float(np.quantile(rel, 0.9)),
+                                 "within_bar": float((rel <= bar).mean())},
+           "wall_limited_points": int((~wall_ok).sum()),
+           "single_instance_seconds_by_side": {str(k): v for k, v in single.items()},
+           "single_instance_points_per_hour": 3600.0 / single_s,
+           "batched_points_per_hour": 3600.0 / batch_s,
+           "training_data_seconds": train_data_s, "train_seconds": train_s,
+           "screen_seconds_per_point": screen_s}
+    if chosen is None:
+        out["accepted_fraction"] = 0.0
+        out["note"] = "no agreement threshold met the bar on the calibration half"
+        f_acc = 0.0
+    else:
+        acc = (spread[ev] <= chosen) & wall_ok[ev]
+        f_acc = float(acc.mean())
+        e = rel[ev][acc]
+        out.update({
+            "agreement_threshold": chosen, "accepted_fraction": f_acc,
+            "accepted_error": {q: float(np.quantile(e, float(q))) for q in ("0.5", "0.9", "0.95", "0.99")}
+            if len(e) else None,
+            "accepted_max_error": float(e.max()) if len(e) else None,
+            "accepted_within_bar": float((e <= bar).mean()) if len(e) else None,
+            "accepted_by_side": {str(int(sd)): float(acc[ste[ev] == sd].mean()) for sd in sides}})
+    mixed_s = screen_s + (1.0 - f_acc) * batch_s
+    m = campaign * n_train
+    campaign_s = train_data_s + train_s + m * mixed_s
+    out.update({
+        "screened_points_per_hour": 3600.0 / mixed_s,
+        "campaign_points": n_train + m,
+        "campaign_points_per_hour": 3600.0 * (n_train + m) / campaign_s,
+        "speedup_batched": single_s / batch_s,
+        "speedup_screened": single_s / mixed_s,
+        "speedup_campaign": single_s * (n_train + m) / campaign_s})
+    if verbose:
+        print(json.dumps(out))
+    return out
+
+
 def label_noise(side=256, steps=20000, points=128, seeds=8, seed=0):
     """Spread of the envelope-velocity label over sigma-field realisations:
     every one of `points` parameter points is run with `seeds` different
@@ -452,6 +664,9 @@ if __name__ == "__main__":
             continue
         if a == "--boundary":
             mode = boundary_gain
+            continue
+        if a == "--validated-sweep":
+            mode = validated_sweep
             continue
         k, _, v = a.lstrip("-").partition("=")
         kw[k] = float(v) if "." in v else int(v)

@@ -35,11 +35,14 @@ def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
                     root / "paper_1301_5058_gb300" / "csrc")
     monkeypatch.setattr(bench, "ROOT", str(root))
     rec = json.load(open(root / "profiles" / "fused_kernel_traffic.json"))
-    want = rec["f32"]["dram_bytes_per_launch_16384sq"]
+    entries = {(e["scheme"], e["noise"]): e["dram_bytes_per_launch_16384sq"] for e in rec["f32"]}
+    want = entries[("euler", "static")]
     assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "static") == want
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "heun", "per-step") == \
+        entries[("heun", "per-step")]
     # another grid, scheme, noise mode or precision: no record
     assert bench.kernel_traffic("f32", "fused_kernel", 4096, 4096, "euler", "static") is None
-    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "heun", "per-step") is None
+    assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "heun", "static") is None
     assert bench.kernel_traffic("f32", "fused_kernel", 16384, 16384, "euler", "per-step") is None
     assert bench.kernel_traffic("f64", "fused_kernel", 16384, 16384, "euler", "static") is None
     # a kernel source that changed since the capture voids the record
@@ -58,5 +61,6 @@ def test_sweep_traffic_record_applies_only_to_its_tuning(tmp_path, monkeypatch):
     tuning = dict(rec["tuning"], graph_steps=64)
     assert bench.sweep_traffic(512, tuning) == rec["dram_bytes_per_launch"]
     assert bench.sweep_traffic(256, tuning) is None                       # another sweep
-    assert bench.sweep_traffic(512, dict(tuning, tile_rows=128)) is None   # other tiles
+    other = 32 if tuning["tile_rows"] != 32 else 64
+    assert bench.sweep_traffic(512, dict(tuning, tile_rows=other)) is None  # other tiles
     assert bench.sweep_traffic(512, dict(tuning, time_block=1)) is None    # one stage per pass

@@ -142,3 +142,22 @@ def test_network_gain_over_solver_only(cx):
     assert t["accepted"] >= 0.5 and t["p95_error"] <= 0.08
     # solver runs saved: points per hour grow by at least 1 / (1 - accepted)
     assert out["speedup_screened"] >= 2.0 * out["speedup_batched_solver_only"]
+
+
+def test_validated_sweep_small(cx):
+    # the validated-throughput measurement end to end on a small mix: every
+    # figure present and consistent; the accepted points (if any) meet the
+    # stated bar at the stated quantile on the evaluation half
+    from paper_1301_5058_gb300 import surrogate
+    out = surrogate.validated_sweep(train_side=128, sides=(96, 128), steps=600, n_train=256,
+                                    n_test=128, members=2, train_steps=1500, decay=1,
+                                    bar=0.05, campaign=1, samples=12)
+    for k in ("single_instance_points_per_hour", "batched_points_per_hour",
+              "screened_points_per_hour", "campaign_points_per_hour"):
+        assert out[k] > 0
+    assert 0.0 <= out["accepted_fraction"] <= 1.0
+    batch_s = 3600.0 / out["batched_points_per_hour"]
+    mixed_s = out["screen_seconds_per_point"] + (1 - out["accepted_fraction"]) * batch_s
+    assert out["screened_points_per_hour"] == pytest.approx(3600.0 / mixed_s, rel=1e-9)
+    if out["accepted_fraction"] > 0:
+        assert out["accepted_error"]["0.5"] <= out["accepted_error"]["0.99"]
