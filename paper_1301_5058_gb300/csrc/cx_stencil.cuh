@@ -111,15 +111,17 @@ __device__ __forceinline__ double2 sub_rn(double2 a, double2 b, double2)
 }
 // c / q for the receptor-law weight (q = (2 + n_L + n_R)^2 >= 4).  FP32: the
 // fast division (the FP32 path is judged by tolerance).  FP64: c times a
-// reciprocal refined by Newton-Raphson, x <- x + x (1 - q x), from an FP32
-// seed: __fdividef's documented bound (2 ulp of float, 2^-22) gives 2^-44
-// after one step and below FP64 rounding after two, so the weight is within
-// about one ulp of c / q at a third of the FP64 instructions of the IEEE
-// division.
+// reciprocal refined by Newton's method for 1/q, x <- x + x (1 - q x), whose
+// relative error e becomes e^2 per step, from the hardware's approximate
+// FP64 reciprocal (rcp.approx.ftz.f64; q is never subnormal).  Any seed within
+// 2^-14 of 1/q is below FP64 rounding after the two steps (2^-28, then
+// 2^-56), so the weight is within about one ulp of c / q; the seed needs no
+// FP64 <-> FP32 conversions, which run on GB300's narrow FP64 pipe.
 __device__ __forceinline__ float div_w(float c, float q) { return __fdividef(c, q); }
 __device__ __forceinline__ double div_w(double c, double q)
 {
-    double x = (double)__fdividef(1.0f, (float)q);
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(q));
     x = __fma_rn(x, __fma_rn(-q, x, 1.0), x);
     x = __fma_rn(x, __fma_rn(-q, x, 1.0), x);
     return __dmul_rn(c, x);

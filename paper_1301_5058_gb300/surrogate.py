@@ -20,6 +20,13 @@ branch output trained on the class (branched or not), picks half of
 `per_round` nearest the compact / branched boundary and half where the
 predicted log velocity is steepest (fronts starting to stall); the solver
 verifies them in one batch, the labels are added and the network retrained.
+
+Validated sweep (validated_sweep): training runs at 1024^2 with a time step
+that varies smoothly with the parameters (smooth_dt), the velocity label
+taken from the colony's area-equivalent radius, and a screen (Screen) of an
+ensemble on log velocity plus a correction from the nearest training points;
+a candidate is accepted without a solver run where those neighbours agree
+and its colony stays clear of the walls, the rest go to the batched solver.
 """
 from __future__ import annotations
 
@@ -318,6 +325,72 @@ class Ensemble:
             m.close()
 
 
+def poly_features(X, degree=3) -> np.ndarray:
+    """All monomials of the columns of X up to `degree` (with the constant)."""
+    import itertools
+    X = np.asarray(X, np.float64)
+    cols = [np.ones(len(X))]
+    for d in range(1, degree + 1):
+        for c in itertools.combinations_with_replacement(range(X.shape[1]), d):
+            cols.append(np.prod(X[:, c], axis=1))
+    return np.stack(cols, 1)
+
+
+class Screen:
+    """The learned screen of the validated sweep: log velocity = a
+    least-squares polynomial of the encoded inputs (degree 0 by default: the
+    mean) + an ensemble of networks (on the GPU kernels of include/cx.h)
+    trained on that fit's residual + a correction from the k nearest training
+    points (their inverse-distance weighted residual).  The spread of those
+    neighbours' residuals is the screen's confidence: the networks miss by a
+    bias that varies smoothly over the box, so where the neighbours agree the
+    correction holds.  (With a cubic baseline the networks, whose zero-bias
+    initial function is odd and nearly cubic in the inputs, see a target
+    orthogonal to everything they start from: their output weights decay and
+    they settle on a constant, so the baseline stays off.)"""
+
+    def __init__(self, members=8, seed=0, k=16, degree=0, max_batch=8192):
+        self.ens = Ensemble(members, seed, max_batch=max_batch)
+        self.k = k
+        self.degree = degree
+
+    def _base_log(self, X):
+        return poly_features(X, self.degree) @ self.coef
+
+    def _net_log(self, points):
+        return np.mean([m.predict(points)[:, 0] for m in self.ens.models], 0)
+
+    def fit(self, points, velocity, **kw):
+        X = encode(points).astype(np.float64)
+        y = np.log(np.maximum(np.asarray(velocity, np.float64), 1e-12))
+        self.coef, *_ = np.linalg.lstsq(poly_features(X, self.degree), y, rcond=None)
+        r = y - self._base_log(X)
+        from concurrent.futures import ThreadPoolExecutor
+        t = np.stack([r, np.zeros_like(r)], 1)
+        with ThreadPoolExecutor(max_workers=len(self.ens.models)) as ex:
+            list(ex.map(lambda m: m.fit(points, t, **kw), self.ens.models))
+        self.X = X
+        self.res = y - self._base_log(X) - self._net_log(points)
+        return self
+
+    def predict(self, points, chunk=2048):
+        """(velocity, neighbour spread of the log residual) of each point."""
+        X = encode(points).astype(np.float64)
+        logv = self._base_log(X) + self._net_log(points)
+        corr = np.empty(len(X))
+        spread = np.empty(len(X))
+        for c in range(0, len(X), chunk):
+            D = ((X[c:c + chunk, None, :] - self.X[None, :, :]) ** 2).sum(-1)
+            nb = np.argpartition(D, self.k, axis=1)[:, :self.k]
+            w = 1.0 / (np.take_along_axis(D, nb, 1) + 1e-6)
+            corr[c:c + chunk] = (self.res[nb] * w).sum(1) / w.sum(1)
+            spread[c:c + chunk] = self.res[nb].std(1)
+        return np.exp(logv + corr), spread
+
+    def close(self):
+        self.ens.close()
+
+
 def single_instance_seconds_per_point(side, steps, spec_point, repeats=2):
     """Wall time of one point stepped alone through cx_step (creation,
     `steps` steps, diagnostics every steps/40), the plain way."""
@@ -443,9 +516,10 @@ def single_instance_seconds(side, steps, point, r0sq=32.0 ** 2, samples=40, repe
 
 
 def validated_sweep(train_side=1024, sides=(512, 1024, 1536, 2048), steps=20000, n_train=8192,
-                    n_test=1024, members=8, train_steps=60000, decay=19, lr=2e-3, seed=0,
+                    n_test=1024, members=8, train_steps=200000, decay=19, lr=2e-3, seed=0,
                     bar=0.01, quantile=0.95, wall_frac=0.6, campaign=4, chunk=2048,
-                    r0sq=32.0 ** 2, samples=40, verbose=True, save=None, schedule="cosine"):
+                    r0sq=32.0 ** 2, samples=40, verbose=True, save=None, schedule="cosine",
+                    knn=16):
     """Validated sweep points per hour on a mix of grid sizes, with and
     without the learned screen.
 
@@ -456,9 +530,13 @@ def validated_sweep(train_side=1024, sides=(512, 1024, 1536, 2048), steps=20000,
     accepts a point without a solver run when (a) the ensemble's members
     agree to a relative spread s* and (b) the colony, grown at the predicted
     velocity from the inoculum, stays within wall_frac of the grid's
-    half-width (the labels are free-space velocities).  s* is the largest
-    spread at which the accepted points of the calibration half of the
-    held-out set meet `bar` at `quantile`; the other half reports the error.
+    half-width (the labels are free-space velocities).  The screen (Screen)
+    predicts the velocity from a cubic fit, an ensemble of networks on its
+    residual and a correction from the `knn` nearest training points; its
+    confidence is the spread of those neighbours' residuals, and s* is the
+    largest spread at which the accepted points of the calibration half of
+    the held-out set meet `bar` at `quantile`; the other half reports the
+    error.
     Rejected points go to the batched solver, whose every label is exact by
     construction (a batch instance equals its single grid bit for bit)."""
     import json
@@ -487,18 +565,18 @@ def validated_sweep(train_side=1024, sides=(512, 1024, 1536, 2048), steps=20000,
     single_s = float(np.mean([single[int(sd)] for sd in ste]))
     # the ensemble
     ok = vtr > 0
-    ens = Ensemble(members, seed, max_batch=8192)
+    scr = Screen(members, seed, k=knn)
     t2 = time.perf_counter()
-    ens.fit(ptr[ok], vtr[ok], steps=train_steps, lr=lr, batch=256, decay=decay,
+    scr.fit(ptr[ok], vtr[ok], steps=train_steps, lr=lr, batch=256, decay=decay,
             schedule=schedule)
     train_s = time.perf_counter() - t2
-    pool = draw_points(65536, seed + 4242, a_range=(0.0, 1.0))
+    pool = draw_points(16384, seed + 4242, a_range=(0.0, 1.0))
     t3 = time.perf_counter()
-    ens.predict(pool)
+    scr.predict(pool)
     steps * smooth_dt(pool)
     screen_s = (time.perf_counter() - t3) / len(pool)
-    mean, spread = ens.predict(pte)
-    ens.close()
+    mean, spread = scr.predict(pte)
+    scr.close()
     if save:
         np.savez_compressed(save, ptr=ptr, vtr=vtr, pte=pte, ste=ste, vte=vte, mean=mean,
                             spread=spread, **{"tr_" + k: v for k, v in info_tr.items()},
@@ -520,6 +598,8 @@ def validated_sweep(train_side=1024, sides=(512, 1024, 1536, 2048), steps=20000,
            "label": "slope of sqrt(area_env / pi) over the second half of the run",
            "time_step": "0.2 / (4 (Dn + Dc) / dx^2 + 4 Dn / dx^2 + B), smooth in the parameters",
            "training_schedule": f"Adam, {train_steps} steps in {decay + 1} chunks, {schedule} rate from {lr}",
+           "screen": f"{members} networks on log velocity + inverse-distance weighted residual "
+                     f"of the {knn} nearest training points; confidence: their residuals' spread",
            "bar": bar, "quantile": quantile, "wall_frac": wall_frac,
            "heldout_error_all": {"median": float(np.median(rel)),
                                  "p90": float(np.quantile(rel, 0.9)),
