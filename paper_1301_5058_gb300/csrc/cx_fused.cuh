@@ -42,7 +42,12 @@ template <int NOISE> constexpr int fused_threads() { return NOISE ? kThreads : 3
 // the end lanes).  nz1 / nz2: the per-step noise of the first and second
 // stage (NOISE 1; nz2 = nz1 under Heun).  INTERIOR: every column the warp
 // holds lies inside the grid, x0 >= 0 and x0 + 4 <= nx for all threads.
-template <typename T, int LAW, int MOB, int NOISE, bool HEUN, int DIR, bool INTERIOR>
+// OFF32: element offsets fit in 32 bits (ny * pitch < 2^31), so each address
+// is one widening multiply-add; measured faster only when sigma is drawn in
+// registers (the per-step passes: Heun 1.036x, Euler 1.017x at 16384^2; the
+// static-sigma passes ran 1-2 % slower).
+template <typename T, int LAW, int MOB, int NOISE, bool HEUN, int DIR, bool INTERIOR,
+          bool OFF32 = false>
 __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long long pitch,
                                        const KV<P2<T>> &k, const NoiseT<T> &nz1,
                                        const NoiseT<T> &nz2, int x0, int j0, int jend)
@@ -106,9 +111,12 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
         constexpr bool STEADY = decltype(steady)::value;
         const int r = rfirst + DIR * p;
         const bool in_r = STEADY || (r >= 0 && r < ny);  // uniform across the block
-        const long long off = (long long)r * pitch + xv;
+        // element offset of this thread's vector in row r (OFF32: in 32 bits)
+        const long long off = OFF32 ? (long long)(r * (int)pitch + (int)xv) : (long long)r * pitch + xv;
         if (DIR > 0 ? r + kPrefetchRows <= plast : r - kPrefetchRows >= plast)
-            prefetch_row<T, NOISE>(P, off + DIR * kPrefetchRows * pitch);
+            prefetch_row<T, NOISE>(P, OFF32 ? (long long)(r * (int)pitch + (int)xv +
+                                                          DIR * kPrefetchRows * (int)pitch)
+                                            : off + DIR * kPrefetchRows * pitch);
         Cells<T> br = zero_cells<T>(), nr = zero_cells<T>(), sr = zero_cells<T>();
         if (in_r) {
             br = vload(P.b + off);
@@ -149,7 +157,7 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
             T vb[kCells], vn[kCells];
             join4(ob, vb);
             join4(on, vn);
-            const long long off = (long long)o * pitch;
+            const long long off = OFF32 ? (long long)(o * (int)pitch) : (long long)o * pitch;
             if (writer) {
                 if (INTERIOR || x0 + kCells <= nx) {
                     Vec<T>::store(P.bo + off + x0, vb);

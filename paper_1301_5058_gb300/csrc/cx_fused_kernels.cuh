@@ -23,7 +23,7 @@ template <typename T> constexpr int fused_min_blocks()
     return sizeof(T) == 4 ? CX_FUSED_MIN_BLOCKS_F32 : 2;
 }
 
-template <typename T, int LAW, int MOB, int NOISE, bool HEUN>
+template <typename T, int LAW, int MOB, int NOISE, bool HEUN, bool OFF32>
 __global__ void __launch_bounds__(fused_threads<NOISE>(),
                                   fused_min_blocks<T>() * (kThreads / fused_threads<NOISE>()))
     fused_kernel(Ptrs<T> P, int nx, int ny, long long pitch, KV<P2<T>> k, NoiseT<T> nz1,
@@ -42,14 +42,18 @@ __global__ void __launch_bounds__(fused_threads<NOISE>(),
     const bool interior = blockIdx.x > 0 && xb + kBlockCols + kCells <= nx;
     if (blockIdx.y & 1) {
         if (interior)
-            march2<T, LAW, MOB, NOISE, HEUN, -1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, -1, true, OFF32>(P, nx, ny, pitch, k, nz1, nz2, x0, j0,
+                                                                 jend);
         else
-            march2<T, LAW, MOB, NOISE, HEUN, -1, false>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, -1, false, OFF32>(P, nx, ny, pitch, k, nz1, nz2, x0, j0,
+                                                                 jend);
     } else {
         if (interior)
-            march2<T, LAW, MOB, NOISE, HEUN, +1, true>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, +1, true, OFF32>(P, nx, ny, pitch, k, nz1, nz2, x0, j0,
+                                                                 jend);
         else
-            march2<T, LAW, MOB, NOISE, HEUN, +1, false>(P, nx, ny, pitch, k, nz1, nz2, x0, j0, jend);
+            march2<T, LAW, MOB, NOISE, HEUN, +1, false, OFF32>(P, nx, ny, pitch, k, nz1, nz2, x0, j0,
+                                                                 jend);
     }
 }
 
@@ -71,8 +75,13 @@ cudaError_t launch_t(const StepArgs &a, cudaStream_t st)
     constexpr int threads = fused_threads<NOISE>();
     constexpr int cols = (threads / 32) * kFusedCols;
     const dim3 grid((a.nx + cols - 1) / cols, (a.ny + a.rows - 1) / a.rows);
-    fused_kernel<T, LAW, MOB, NOISE, HEUN><<<grid, threads, 0, st>>>(P, a.nx, a.ny, a.pitch, k,
-                                                                      nz1, nz2, a.rows);
+    // 32-bit element offsets for the per-step passes when every offset fits
+    if (NOISE == 1 && (long long)a.ny * a.pitch < (1LL << 31))
+        fused_kernel<T, LAW, MOB, NOISE, HEUN, NOISE == 1><<<grid, threads, 0, st>>>(
+            P, a.nx, a.ny, a.pitch, k, nz1, nz2, a.rows);
+    else
+        fused_kernel<T, LAW, MOB, NOISE, HEUN, false><<<grid, threads, 0, st>>>(
+            P, a.nx, a.ny, a.pitch, k, nz1, nz2, a.rows);
     return cudaGetLastError();
 }
 
