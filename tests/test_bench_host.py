@@ -26,13 +26,26 @@ def test_flop_count_of_the_scheme():
     assert bench.FLOPS_PER_CELL_UPDATE == {"euler": 43, "heun": 90}
 
 
-def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
-    # a copy of the repository's records in a scratch root, so that source
-    # edits can be simulated without touching the tree
+def _scratch_root(tmp_path):
+    """A copy of the repository's records and kernel sources in a scratch
+    root, with each record's source hashes set to the copied sources, so that
+    the matching logic is tested whether or not the records are current and
+    source edits can be simulated without touching the tree."""
+    import hashlib
     root = tmp_path / "repo"
     shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
-    shutil.copytree(os.path.join(ROOT, "paper_1301_5058_gb300", "csrc"),
-                    root / "paper_1301_5058_gb300" / "csrc")
+    csrc = root / "paper_1301_5058_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_1301_5058_gb300", "csrc"), csrc)
+    for rec_path in (root / "profiles").glob("*_traffic.json"):
+        rec = json.load(open(rec_path))
+        rec["sources_sha256_16"] = {f: hashlib.sha256((csrc / f).read_bytes()).hexdigest()[:16]
+                                    for f in rec["sources_sha256_16"]}
+        json.dump(rec, open(rec_path, "w"))
+    return root
+
+
+def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
+    root = _scratch_root(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
     rec = json.load(open(root / "profiles" / "fused_kernel_traffic.json"))
     entries = {(e["scheme"], e["noise"]): e["dram_bytes_per_launch_16384sq"] for e in rec["f32"]}
@@ -52,10 +65,7 @@ def test_traffic_record_applies_only_to_its_run(tmp_path, monkeypatch):
 
 
 def test_sweep_traffic_record_applies_only_to_its_tuning(tmp_path, monkeypatch):
-    root = tmp_path / "repo"
-    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
-    shutil.copytree(os.path.join(ROOT, "paper_1301_5058_gb300", "csrc"),
-                    root / "paper_1301_5058_gb300" / "csrc")
+    root = _scratch_root(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
     rec = json.load(open(root / "profiles" / "batch_fused_kernel_traffic.json"))["f32"]
     tuning = dict(rec["tuning"], graph_steps=64)
