@@ -84,3 +84,45 @@ def test_batch_key_names_the_size_mix():
     key = autotune.batch_key([G(512), G(1024), G(512)], [P()])
     assert key == "batch/p1/s0/512x512:2,1024x1024:1"          # sizes in numeric order
     assert json.dumps(key)
+
+
+def test_smooth_time_step_stays_below_the_stability_limit():
+    # the sweep's time step is never above the library's limit (the runs stay
+    # stable), is within a factor 3 of it, and has no kink where the limit's
+    # max / min switch branches (a finite-difference second derivative along
+    # a line through such a switch stays bounded)
+    from paper_1301_5058_gb300 import _build
+    _build.build()
+    import paper_1301_5058_gb300 as cx
+    pts = surrogate.draw_points(400, seed=11, a_range=(0.0, 1.0))
+    sd = surrogate.smooth_dt(pts)
+    g = cx.cx_grid(8, 8, 1.0)
+    for p, d in zip(pts, sd):
+        prm = cx.cx_params_default(n0=p[0], chi0=p[1], sigma0=p[2], noise_amp=p[3], bM=0.71)
+        lim = prm.cfl_frac * cx.cx_dt_limit(g, prm)
+        assert 0.3 * lim <= d <= lim
+    # along sigma0 the library's diffusivity switches from Dn to the cross
+    # diffusivity (a kink of the limit); the smooth step's curvature stays small
+    s0 = np.linspace(0.2, 3.0, 2001)
+    line = np.stack([np.full_like(s0, 0.3), np.zeros_like(s0), s0, np.zeros_like(s0)], 1)
+    y = np.log(surrogate.smooth_dt(line))
+    d2 = np.diff(y, 2) / (s0[1] - s0[0]) ** 2
+    assert np.max(np.abs(d2)) < 10.0
+
+
+def test_initial_area_radius_is_the_disc_above_the_level():
+    # bM exp(-r^2 / r0sq) >= 0.1 n0  <=>  r^2 <= r0sq ln(bM / (0.1 n0))
+    n0 = np.array([0.1, 0.35, 1.5, 7.1])
+    r = surrogate.initial_area_radius(n0, 32.0 ** 2)
+    for ni, ri in zip(n0, r):
+        if 0.71 > 0.1 * ni:
+            assert 0.71 * math.exp(-ri ** 2 / 32.0 ** 2) == pytest.approx(0.1 * ni, rel=1e-12)
+        else:
+            assert ri == 0.0
+
+
+def test_poly_features_span_the_monomials():
+    X = np.random.default_rng(0).uniform(-1, 1, (50, 4))
+    F = surrogate.poly_features(X, 3)
+    assert F.shape == (50, 35)          # C(4 + 3, 3) monomials of degree <= 3
+    assert np.allclose(F[:, 0], 1.0) and np.allclose(F[:, 1:5], X)
