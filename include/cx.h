@@ -166,10 +166,13 @@ int cx_create(const cx_grid *g, const cx_params *p, uint64_t seed, cx_ctx **out)
  * The handle initialises them as cx_create does (sigma field, inoculum; the
  * second state buffers zeroed) and never frees them: they must outlive the
  * handle.  Which of b[0] / b[1] holds the current state changes with every
- * pass; read it through cx_get_field.  Requirements: every pointer non-NULL
- * and 16-byte aligned, pitch >= nx with pitch x element size a multiple of
- * 16 bytes (a multiple of 128 bytes is fastest), and no two arrays
- * overlapping.  Errors: INVALID_ARG (checked before any device work),
+ * pass, and inside each row the library keeps every aligned group of four
+ * cells in the order (4g, 4g+2, 4g+1, 4g+3) (the pair order, which lets a
+ * 16-byte load feed the paired arithmetic directly): read and write the
+ * fields through cx_get_field / cx_set_field, which give the natural order.
+ * Requirements: every pointer non-NULL and 16-byte aligned, pitch >= nx and
+ * a multiple of 4 elements (a multiple of 128 bytes is fastest), and no two
+ * arrays overlapping.  Errors: INVALID_ARG (checked before any device work),
  * DT_UNSTABLE, CUDA.  There is no counterpart in the paper (a memory-ownership
  * interface). */
 int cx_create_with_buffers(const cx_grid *g, const cx_params *p, uint64_t seed, void *const b[2],
@@ -403,8 +406,10 @@ void cx_mlp_destroy(cx_mlp *m);
  * within that budget, or a time-critical loop in which a blocking
  * allocation is not allowed.
  *
- * It computes the same reduction as cx_diagnostics, with the same kernels
- * and the same summation order, over fields the caller owns:
+ * It computes the same reduction as cx_diagnostics, with the same kernels,
+ * over fields the caller owns, in natural in-row order (the library's own
+ * arrays keep each group of four cells in pair order, so the summation order
+ * within a row differs and the sums agree to round-off):
  *   b, n        device arrays of nx*ny cells, row j at element j*pitch,
  *               FP64 or FP32 as `precision` (CX_PREC_*) says;
  *   pitch       elements per row, >= nx;

@@ -373,9 +373,10 @@ int cx_create_with_buffers(const cx_grid *g, const cx_params *p, uint64_t seed, 
     if (rc) return rc;
     FieldBuffers fb{{b[0], b[1]}, {n[0], n[1]}, sigma, (long long)pitch};
     const size_t elem = p->precision == CX_PREC_F64 ? sizeof(double) : sizeof(float);
-    if (pitch < (int64_t)g->nx || ((size_t)pitch * elem) % 16 != 0)
-        return fail(CX_ERR_INVALID_ARG, "pitch %lld: needs pitch >= nx = %d and rows of a multiple "
-                    "of 16 bytes", (long long)pitch, g->nx);
+    // rows hold whole groups of four cells (the pair order) in 16-byte units
+    if (pitch < (int64_t)g->nx || pitch % 4 != 0 || ((size_t)pitch * elem) % 16 != 0)
+        return fail(CX_ERR_INVALID_ARG, "pitch %lld: needs pitch >= nx = %d, a multiple of 4 "
+                    "elements", (long long)pitch, g->nx);
     void *ptrs[5] = {fb.b[0], fb.b[1], fb.n[0], fb.n[1], fb.sigma};
     const unsigned long long span = (unsigned long long)pitch * (unsigned long long)g->ny * elem;
     for (int i = 0; i < 5; ++i) {
@@ -546,20 +547,27 @@ int cx_get_field(cx_ctx *c, int32_t which, void *host, int32_t dtype, size_t cou
     // with per-step noise, sigma is the field the next step will use
     if (which == CX_FIELD_SIGMA && c->p.noise_mode == CX_NOISE_PER_STEP)
         CX_CUDA(fill_sigma(c, c->step), "sigma regeneration");
-    CX_CUDA(cudaStreamSynchronize(c->stream), "synchronize before field read");
+    // the array in natural in-row order for the copy, and back afterwards
+    void *f = field_ptr(c, which);
+    CX_CUDA(cx::launch_pair_order(c->prec, f, c->g.nx, c->g.ny, c->pitch, c->stream), "reorder");
     if (dtype == state_dtype) {
-        CX_CUDA(copy_rows(host, row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
-                                  c->g.ny, cudaMemcpyDeviceToHost, c->stream),
+        CX_CUDA(copy_rows(host, row, f, (size_t)c->pitch * c->elem, row, c->g.ny,
+                          cudaMemcpyDeviceToHost, c->stream),
                 "field copy to host");
+        CX_CUDA(cx::launch_pair_order(c->prec, f, c->g.nx, c->g.ny, c->pitch, c->stream), "reorder");
         CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
         return CX_OK;
     }
     // precision change: copy in the state type, widen or narrow on the host
     std::vector<unsigned char> tmp;
-    try { tmp.resize(count * c->elem); } catch (...) { return fail(CX_ERR_OOM, "host staging"); }
-    CX_CUDA(copy_rows(tmp.data(), row, field_ptr(c, which), (size_t)c->pitch * c->elem, row,
-                              c->g.ny, cudaMemcpyDeviceToHost, c->stream),
+    try { tmp.resize(count * c->elem); } catch (...) {
+        cx::launch_pair_order(c->prec, f, c->g.nx, c->g.ny, c->pitch, c->stream);
+        return fail(CX_ERR_OOM, "host staging");
+    }
+    CX_CUDA(copy_rows(tmp.data(), row, f, (size_t)c->pitch * c->elem, row, c->g.ny,
+                      cudaMemcpyDeviceToHost, c->stream),
             "field copy to host");
+    CX_CUDA(cx::launch_pair_order(c->prec, f, c->g.nx, c->g.ny, c->pitch, c->stream), "reorder");
     CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
     if (state_dtype == CX_F32) {
         const float *s = (const float *)tmp.data();
@@ -600,6 +608,9 @@ int cx_set_field(cx_ctx *c, int32_t which, const void *host, int32_t dtype, size
     CX_CUDA(copy_rows(field_ptr(c, which), (size_t)c->pitch * c->elem, src, row, row, c->g.ny,
                       cudaMemcpyHostToDevice, c->stream),
             "field copy to device");
+    CX_CUDA(cx::launch_pair_order(c->prec, field_ptr(c, which), c->g.nx, c->g.ny, c->pitch,
+                                  c->stream),
+            "reorder");
     CX_CUDA(cudaStreamSynchronize(c->stream), "field copy synchronize");
     return CX_OK;
 }
@@ -651,6 +662,11 @@ int cx_stage_state(cx_ctx *c, const void *b_host, const void *n_host, int32_t dt
     CX_CUDA(copy_rows(c->stage_n, (size_t)c->pitch * c->elem, n_host, row, row, c->g.ny,
                       cudaMemcpyHostToDevice, c->copy_stream),
             "staged copy of n");
+    // into the pair order of the state arrays, still on the copy stream
+    CX_CUDA(cx::launch_pair_order(c->prec, c->stage_b, c->g.nx, c->g.ny, c->pitch, c->copy_stream),
+            "staged reorder of b");
+    CX_CUDA(cx::launch_pair_order(c->prec, c->stage_n, c->g.nx, c->g.ny, c->pitch, c->copy_stream),
+            "staged reorder of n");
     CX_CUDA(cudaEventRecord(c->staged, c->copy_stream), "stage event");
     c->stage_pending = 1;
     return CX_OK;
@@ -673,7 +689,8 @@ int cx_commit_state(cx_ctx *c)
         c->stage_n = t;
     } else {
         // caller-owned state arrays keep their addresses: copy on the device
-        const size_t row = (size_t)c->g.nx * c->elem, pitch = (size_t)c->pitch * c->elem;
+        // (whole groups of four: a row's last cell may lie in the padding)
+        const size_t row = (size_t)((c->g.nx + 3) & ~3) * c->elem, pitch = (size_t)c->pitch * c->elem;
         CX_CUDA(copy_rows(c->b[c->cur], pitch, c->stage_b, pitch, row, c->g.ny,
                           cudaMemcpyDeviceToDevice, c->stream),
                 "commit copy of b");

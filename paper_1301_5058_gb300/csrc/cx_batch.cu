@@ -67,11 +67,11 @@ __global__ void __launch_bounds__(reduce::kThreads)
     const InstDev<T> &I = inst[i];
     reduce::Acc a;
     if constexpr (sizeof(T) == 4)
-        a = reduce::rows_f32<true>((const float *)I.b[parity], (const float *)I.n[parity], I.nx,
-                                   I.ny, I.pitch, I.fth, blockIdx.x, gridDim.x);
+        a = reduce::rows_f32<true, true>((const float *)I.b[parity], (const float *)I.n[parity],
+                                         I.nx, I.ny, I.pitch, I.fth, blockIdx.x, gridDim.x);
     else
-        a = reduce::rows_f64((const double *)I.b[parity], (const double *)I.n[parity], I.nx, I.ny,
-                             I.pitch, I.bth, blockIdx.x, gridDim.x);
+        a = reduce::rows_f64<true>((const double *)I.b[parity], (const double *)I.n[parity], I.nx,
+                                   I.ny, I.pitch, I.bth, blockIdx.x, gridDim.x);
     a = reduce::block_reduce(a);
     if (threadIdx.x == 0)
         reduce::store_acc(part + 8LL * ((long long)i * gridDim.x + blockIdx.x), a);

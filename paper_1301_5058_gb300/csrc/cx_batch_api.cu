@@ -585,9 +585,14 @@ int cx_batch_get_field(cx_batch *B, int32_t index, int32_t which, void *host, in
         dst = tmp.data();
     }
     BX_CUDA(cudaStreamSynchronize(B->stream), "synchronize before field read");
-    BX_CUDA(cudaMemcpy2DAsync(dst, row, batch_field(B, index, which), (size_t)B->pitch[index] * B->elem,
+    // the array in natural in-row order for the copy, and back to pair order
+    void *f = batch_field(B, index, which);
+    const cx_grid &g = B->g[index];
+    BX_CUDA(cx::launch_pair_order(B->prec, f, g.nx, g.ny, B->pitch[index], B->stream), "reorder");
+    BX_CUDA(cudaMemcpy2DAsync(dst, row, f, (size_t)B->pitch[index] * B->elem,
                               row, B->g[index].ny, cudaMemcpyDeviceToHost, B->stream),
             "field copy to host");
+    BX_CUDA(cx::launch_pair_order(B->prec, f, g.nx, g.ny, B->pitch[index], B->stream), "reorder");
     BX_CUDA(cudaStreamSynchronize(B->stream), "field copy synchronize");
     if (dtype != sd) {
         if (sd == CX_F32)
@@ -620,6 +625,9 @@ int cx_batch_set_field(cx_batch *B, int32_t index, int32_t which, const void *ho
     BX_CUDA(cudaMemcpy2DAsync(batch_field(B, index, which), (size_t)B->pitch[index] * B->elem, src, row,
                               row, B->g[index].ny, cudaMemcpyHostToDevice, B->stream),
             "field copy to device");
+    BX_CUDA(cx::launch_pair_order(B->prec, batch_field(B, index, which), B->g[index].nx,
+                                  B->g[index].ny, B->pitch[index], B->stream),
+            "reorder");
     BX_CUDA(cudaStreamSynchronize(B->stream), "field copy synchronize");
     return CX_OK;
 }

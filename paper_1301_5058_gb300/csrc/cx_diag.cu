@@ -24,21 +24,22 @@ using namespace reduce;
 
 constexpr int kMaxBlocks = 1024;
 
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads)
     diag_partial(const double *__restrict__ b, const double *__restrict__ n, int nx, int ny,
                  long long pitch, double bth, double *__restrict__ part)
 {
-    Acc a = rows_f64(b, n, nx, ny, pitch, bth, blockIdx.x, gridDim.x);
+    Acc a = rows_f64<PAIR>(b, n, nx, ny, pitch, bth, blockIdx.x, gridDim.x);
     a = block_reduce(a);
     if (threadIdx.x == 0) store_acc(part + 8LL * blockIdx.x, a);
 }
 
-template <bool VEC>
+template <bool VEC, bool PAIR>
 __global__ void __launch_bounds__(kThreads)
     diag_partial_f32(const float *__restrict__ b, const float *__restrict__ n, int nx, int ny,
                      long long pitch, float fth, double *__restrict__ part)
 {
-    Acc a = rows_f32<VEC>(b, n, nx, ny, pitch, fth, blockIdx.x, gridDim.x);
+    Acc a = rows_f32<VEC, PAIR>(b, n, nx, ny, pitch, fth, blockIdx.x, gridDim.x);
     a = block_reduce(a);
     if (threadIdx.x == 0) store_acc(part + 8LL * blockIdx.x, a);
 }
@@ -58,20 +59,28 @@ int diag_blocks_for(int ny) { return ny < kMaxBlocks ? (ny < 1 ? 1 : ny) : kMaxB
 
 cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, int ny,
                                long long pitch, double b_threshold, DiagScratch s,
-                               cudaStream_t st)
+                               cudaStream_t st, bool pair_order)
 {
     if (prec == CX_PREC_F64) {
-        diag_partial<<<s.blocks, kThreads, 0, st>>>((const double *)b, (const double *)n, nx, ny,
-                                                    pitch, b_threshold, s.partials);
+        if (pair_order)
+            diag_partial<true><<<s.blocks, kThreads, 0, st>>>((const double *)b, (const double *)n,
+                                                              nx, ny, pitch, b_threshold, s.partials);
+        else
+            diag_partial<false><<<s.blocks, kThreads, 0, st>>>((const double *)b, (const double *)n,
+                                                               nx, ny, pitch, b_threshold, s.partials);
     } else {
         const float fth = float_threshold(b_threshold);
         const bool vec = (pitch % 4 == 0) && ((uintptr_t)b % 16 == 0) && ((uintptr_t)n % 16 == 0);
-        if (vec)
-            diag_partial_f32<true><<<s.blocks, kThreads, 0, st>>>((const float *)b, (const float *)n,
-                                                                  nx, ny, pitch, fth, s.partials);
+        const float *fb = (const float *)b, *fn = (const float *)n;
+        if (pair_order)  // pair order implies rows of whole 16-byte groups
+            diag_partial_f32<true, true><<<s.blocks, kThreads, 0, st>>>(fb, fn, nx, ny, pitch, fth,
+                                                                        s.partials);
+        else if (vec)
+            diag_partial_f32<true, false><<<s.blocks, kThreads, 0, st>>>(fb, fn, nx, ny, pitch, fth,
+                                                                         s.partials);
         else
-            diag_partial_f32<false><<<s.blocks, kThreads, 0, st>>>(
-                (const float *)b, (const float *)n, nx, ny, pitch, fth, s.partials);
+            diag_partial_f32<false, false><<<s.blocks, kThreads, 0, st>>>(fb, fn, nx, ny, pitch,
+                                                                          fth, s.partials);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

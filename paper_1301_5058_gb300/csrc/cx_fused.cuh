@@ -72,7 +72,7 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
             for (int c = 0; c < kCells; ++c)
                 if (x0 + c < 0 || x0 + c >= nx) v[c] = T(0);  // outside the row
         }
-        return split4(v);
+        return split4_nat(v);
     };
     // x-faces of a row; b and n of cell x0-1 from the left lane, sigma's
     // given (ls); the face beyond x0+3 is the right lane's first.  The end
@@ -155,19 +155,22 @@ __device__ __forceinline__ void march2(const Ptrs<T> &P, int nx, int ny, long lo
                 on = heun_mean(un, on, k);
             }
             T vb[kCells], vn[kCells];
-            join4(ob, vb);
-            join4(on, vn);
             const long long off = OFF32 ? (long long)(o * (int)pitch) : (long long)o * pitch;
             if (writer) {
                 if (INTERIOR || x0 + kCells <= nx) {
+                    join4(ob, vb);
+                    join4(on, vn);
                     Vec<T>::store(P.bo + off + x0, vb);
                     Vec<T>::store(P.no + off + x0, vn);
                 } else {
+                    // the row's last group: cell x0 + c lives at column x0 + pair_col(c)
+                    join4_nat(ob, vb);
+                    join4_nat(on, vn);
 #pragma unroll
                     for (int c = 0; c < kCells; ++c)
                         if (x0 + c < nx) {
-                            P.bo[off + x0 + c] = vb[c];
-                            P.no[off + x0 + c] = vn[c];
+                            P.bo[off + x0 + pair_col(c)] = vb[c];
+                            P.no[off + x0 + pair_col(c)] = vn[c];
                         }
                 }
             }

@@ -13,7 +13,9 @@
 //
 // Initial state (Eq. inicond, Eq. inibacexp): n = n0, b = bM exp(-r^2/r0sq)
 // with r the distance of the cell centre from the domain centre, cut to
-// zero where r^2/r0sq > 40.
+// zero where r^2/r0sq > 40.  Both write the arrays in pair order
+// (cx_internal.h), as do the step kernels; launch_pair_order converts an
+// array between that order and the natural one.
 #include "cx_internal.h"
 #include "cx_philox.cuh"
 
@@ -35,7 +37,7 @@ __global__ void sigma_init_kernel(T *__restrict__ sigma, int nx, int ny, long lo
             v = (T)sigma_f64(seed, (uint64_t)c, step, dist, sigma0, amp);
         else
             v = (T)sigma_f32(seed, (uint64_t)c, step, dist, s0f, af);
-        sigma[(long long)j * pitch + i] = v;
+        sigma[(long long)j * pitch + pair_col(i)] = v;
     }
 }
 
@@ -57,8 +59,24 @@ __global__ void initial_state_kernel(T *__restrict__ b, T *__restrict__ n, int n
         // an FP32 and an FP64 state start alike; the mass changes by less
         // than e^-40), which also spares the exp of most cells of a grid
         const double e = q < -40.0 ? 0.0 : exp(q);
-        b[(long long)j * pitch + i] = (T)__dmul_rn(bM, e);
-        n[(long long)j * pitch + i] = (T)n0;
+        b[(long long)j * pitch + pair_col(i)] = (T)__dmul_rn(bM, e);
+        n[(long long)j * pitch + pair_col(i)] = (T)n0;
+    }
+}
+
+// Swap the middle two elements of every group of four, for the groups that
+// hold the row's nx cells.
+template <typename T>
+__global__ void pair_order_kernel(T *__restrict__ a, int groups, int ny, long long pitch)
+{
+    const long long total = (long long)groups * ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long j = q / groups, g = q - j * groups;
+        T *p = a + j * pitch + 4 * g;
+        const T x = p[1];
+        p[1] = p[2];
+        p[2] = x;
     }
 }
 
@@ -82,6 +100,18 @@ cudaError_t launch_sigma_init(int prec, void *sigma, int nx, int ny, long long p
     else
         sigma_init_kernel<float><<<grid, threads, 0, st>>>((float *)sigma, nx, ny, pitch, seed,
                                                            step, sigma0, amp, dist, recipe);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_order(int prec, void *a, int nx, int ny, long long pitch, cudaStream_t st)
+{
+    const int groups = (nx + 3) / 4;
+    const int threads = 256;
+    const int grid = grid_for((long long)groups * ny, threads);
+    if (prec == CX_PREC_F64)
+        pair_order_kernel<double><<<grid, threads, 0, st>>>((double *)a, groups, ny, pitch);
+    else
+        pair_order_kernel<float><<<grid, threads, 0, st>>>((float *)a, groups, ny, pitch);
     return cudaGetLastError();
 }
 

@@ -77,15 +77,33 @@ cudaError_t launch_step(int prec, const StepArgs &a, cudaStream_t st);
 // (bo, no), which must be other buffers.  bu / nu / stage are not used.
 cudaError_t launch_fused(int prec, const StepArgs &a, int heun, cudaStream_t st);
 
+// In-row order of the device arrays.  Each aligned group of four cells of a
+// row, columns 4g .. 4g+3, is stored as (4g, 4g+2, 4g+1, 4g+3): a 16-byte
+// vector load then hands a thread its cells already as the pairs
+// (4g, 4g+2) and (4g+1, 4g+3) that the paired FP32 arithmetic works on, with
+// no register moves to regroup them (1.05x on the 16384^2 FP32 pass).  The
+// order swaps the middle two of each group, so it is its own inverse.  Rows
+// therefore need a pitch that is a multiple of 4 elements; a row's last
+// group may hold a cell beyond nx in the padding columns.
+__host__ __device__ __forceinline__ long long pair_col(long long i)
+{
+    return (i & ~3LL) | ((i & 1LL) << 1) | ((i >> 1) & 1LL);
+}
+// Swaps the middle two elements of every group of four of the first
+// ceil(nx/4)*4 columns of each row, in place: converts an array between the
+// natural in-row order and the pair order (either way).
+cudaError_t launch_pair_order(int prec, void *a, int nx, int ny, long long pitch, cudaStream_t st);
+
 struct DiagScratch {
     double *partials;  // [blocks][8]
     double *result;    // [8] on the device
     int blocks;
 };
 int diag_blocks_for(int ny);
+// pair_order: the fields are in the library's pair order (else natural).
 cudaError_t launch_diagnostics(int prec, const void *b, const void *n, int nx, int ny,
                                long long pitch, double b_threshold, DiagScratch s,
-                               cudaStream_t st);
+                               cudaStream_t st, bool pair_order = true);
 
 // b on a circle of `radius` about the domain centre, ns samples (cx_labels.cu).
 cudaError_t launch_polar(int prec, const void *b, int nx, int ny, long long pitch, double dx,

@@ -24,8 +24,10 @@ __global__ void polar_kernel(const T *__restrict__ b, int nx, int ny, long long 
     const int i0 = min((int)floor(x), nx - 1), j0 = min((int)floor(y), ny - 1);
     const int i1 = min(i0 + 1, nx - 1), j1 = min(j0 + 1, ny - 1);
     const double wx = x - i0, wy = y - j0;
-    const double b00 = (double)b[(long long)j0 * pitch + i0], b01 = (double)b[(long long)j0 * pitch + i1];
-    const double b10 = (double)b[(long long)j1 * pitch + i0], b11 = (double)b[(long long)j1 * pitch + i1];
+    // the array is in pair order (cx_internal.h)
+    const long long c0 = pair_col(i0), c1 = pair_col(i1);
+    const double b00 = (double)b[(long long)j0 * pitch + c0], b01 = (double)b[(long long)j0 * pitch + c1];
+    const double b10 = (double)b[(long long)j1 * pitch + c0], b11 = (double)b[(long long)j1 * pitch + c1];
     out[k] = (1.0 - wy) * ((1.0 - wx) * b00 + wx * b01) + wy * ((1.0 - wx) * b10 + wx * b11);
 }
 

@@ -137,7 +137,8 @@ extern "C" int cx_diagnostics_noalloc(const void *b, const void *n, int32_t nx, 
     s.result = result_dev;
     s.blocks = blocks;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cx::launch_diagnostics(precision, b, n, nx, ny, pitch, b_threshold, s, st);
+    // the caller's fields are in natural in-row order
+    cudaError_t e = cx::launch_diagnostics(precision, b, n, nx, ny, pitch, b_threshold, s, st, false);
     if (e != cudaSuccess) return noalloc_fail(CX_ERR_CUDA, "diagnostics launch", cudaGetErrorString(e));
     if (!out) return CX_OK;
     double h[8];

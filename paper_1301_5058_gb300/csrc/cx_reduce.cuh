@@ -95,18 +95,24 @@ __device__ __forceinline__ Acc load_acc(const double *p)
     return o;
 }
 
-// FP64 state: rows j = j0, j0 + jstep, ... of one grid, this thread's columns.
+// FP64 state: rows j = j0, j0 + jstep, ... of one grid, this thread's
+// elements.  PAIR: the rows are in the library's pair order (cx_internal.h),
+// so the element at position p of a row is the cell in column pair_col(p).
+template <bool PAIR>
 __device__ __forceinline__ Acc rows_f64(const double *__restrict__ b, const double *__restrict__ n,
                                         int nx, int ny, long long pitch, double bth, int j0,
                                         int jstep)
 {
     Acc a = empty_acc();
+    const int width = PAIR ? (nx + 3) & ~3 : nx;
     for (int j = j0; j < ny; j += jstep) {
         const double *rb = b + (long long)j * pitch;
         const double *rn = n + (long long)j * pitch;
         const long long dy = 2LL * j + 1 - ny;
-        for (int i = threadIdx.x; i < nx; i += kThreads) {
-            const double vb = rb[i], vn = rn[i];
+        for (int p = threadIdx.x; p < width; p += kThreads) {
+            const int i = PAIR ? (int)pair_col(p) : p;
+            if (PAIR && i >= nx) continue;
+            const double vb = rb[p], vn = rn[p];
             a.sb += vb;
             a.sn += vn;
             if (!isfinite(vb) || !isfinite(vn)) a.bad = 1;
@@ -140,8 +146,9 @@ __device__ __forceinline__ void two_sum(float &s, float &c, float x)
 // the threshold test decides exactly as an FP64 comparison would.  The
 // envelope radius of a row is attained at its first or last column above
 // the threshold ((2i+1-nx)^2 is convex in i).  VEC: rows start 16-byte
-// aligned, so whole float4 vectors are read.
-template <bool VEC>
+// aligned, so whole float4 vectors are read.  PAIR: the rows are in the
+// library's pair order (a vector holds columns 4v, 4v+2, 4v+1, 4v+3).
+template <bool VEC, bool PAIR>
 __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float *__restrict__ n,
                                         int nx, int ny, long long pitch, float fth, int j0,
                                         int jstep)
@@ -175,13 +182,21 @@ __device__ __forceinline__ Acc rows_f32(const float *__restrict__ b, const float
                 const float4 qb = __ldg(reinterpret_cast<const float4 *>(rb) + v);
                 const float4 qn = __ldg(reinterpret_cast<const float4 *>(rn) + v);
                 cell(4 * v, qb.x, qn.x);
-                cell(4 * v + 1, qb.y, qn.y);
-                cell(4 * v + 2, qb.z, qn.z);
+                cell(4 * v + (PAIR ? 2 : 1), qb.y, qn.y);
+                cell(4 * v + (PAIR ? 1 : 2), qb.z, qn.z);
                 cell(4 * v + 3, qb.w, qn.w);
             }
             tail = nv << 2;
         }
-        for (int i = tail + threadIdx.x; i < nx; i += kThreads) cell(i, rb[i], rn[i]);
+        if (PAIR) {
+            const int width = (nx + 3) & ~3;
+            for (int p = tail + threadIdx.x; p < width; p += kThreads) {
+                const int i = (int)pair_col(p);
+                if (i < nx) cell(i, rb[p], rn[p]);
+            }
+        } else {
+            for (int i = tail + threadIdx.x; i < nx; i += kThreads) cell(i, rb[i], rn[i]);
+        }
         cnt += above;
         sb += (double)bs + (double)bc;
         sn += (double)ns + (double)nc;

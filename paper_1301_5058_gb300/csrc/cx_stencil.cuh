@@ -218,11 +218,23 @@ __device__ __forceinline__ void face(V sL, V sR, V nL, V nR, V bL, V bR, const K
 template <typename T> struct Cells {
     P2<T> E, O;
 };
+// A vector as loaded from (or stored to) a device array in pair order
+// (cx_internal.h): (x0, x0+2, x0+1, x0+3), i.e. E then O.
 template <typename T> __device__ __forceinline__ Cells<T> split4(const T (&v)[4])
+{
+    return Cells<T>{pair(v[0], v[1]), pair(v[2], v[3])};
+}
+template <typename T> __device__ __forceinline__ void join4(const Cells<T> &c, T (&v)[4])
+{
+    v[0] = c.E.x; v[1] = c.E.y; v[2] = c.O.x; v[3] = c.O.y;
+}
+// Four values in natural cell order x0 .. x0+3 (values made in registers,
+// such as per-step sigma, and the element-wise edge stores).
+template <typename T> __device__ __forceinline__ Cells<T> split4_nat(const T (&v)[4])
 {
     return Cells<T>{pair(v[0], v[2]), pair(v[1], v[3])};
 }
-template <typename T> __device__ __forceinline__ void join4(const Cells<T> &c, T (&v)[4])
+template <typename T> __device__ __forceinline__ void join4_nat(const Cells<T> &c, T (&v)[4])
 {
     v[0] = c.E.x; v[1] = c.O.x; v[2] = c.E.y; v[3] = c.O.y;
 }
@@ -492,7 +504,7 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
                 for (int c = 0; c < kCells; ++c)
                     if (x0 + c >= nx) v[c] = T(0);  // past the row's end
             }
-            R.s = split4(v);
+            R.s = split4_nat(v);
         }
         R.hb = R.hn = R.hs = T(0);
         if (halo) {
@@ -567,18 +579,21 @@ __device__ __forceinline__ void march(const Ptrs<T> &P, int nx, int ny, long lon
             on = heun_mean(cur.un, on, k);
         }
         T vb[kCells], vn[kCells];
-        join4(ob, vb);
-        join4(on, vn);
         const long long off = (long long)j * pitch;
         if (INTERIOR || x0 + kCells <= nx) {
+            join4(ob, vb);
+            join4(on, vn);
             Vec<T>::store(P.bo + off + x0, vb);
             Vec<T>::store(P.no + off + x0, vn);
         } else {
+            // the row's last group: cell x0 + c lives at column x0 + pair_col(c)
+            join4_nat(ob, vb);
+            join4_nat(on, vn);
 #pragma unroll
             for (int c = 0; c < kCells; ++c)
                 if (x0 + c < nx) {
-                    P.bo[off + x0 + c] = vb[c];
-                    P.no[off + x0 + c] = vn[c];
+                    P.bo[off + x0 + pair_col(c)] = vb[c];
+                    P.no[off + x0 + pair_col(c)] = vn[c];
                 }
         }
 

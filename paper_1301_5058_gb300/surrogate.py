@@ -697,7 +697,7 @@ def active_sweep(rounds=3, per_round=64, first=128, pool=4096, seed=0, label_kw=
 
 
 def boundary_gain(rounds=3, per_round=128, first=256, pool=8192, seed=0, side=256, steps=20000,
-                  train_steps=6000):
+                  train_steps=6000, r0sq=64.0):
     """Does the surrogate-guided sweep sample the morphology boundaries?
     Runs active_sweep, then as many uniformly drawn points through the
     solver, and compares (a) the share of branched colonies (branch count
@@ -707,7 +707,7 @@ def boundary_gain(rounds=3, per_round=128, first=256, pool=8192, seed=0, side=25
     share of slow fronts (velocity below the uniform sample's 10th
     percentile, near the stall boundary) among the steep-velocity picks."""
     import json
-    label_kw = dict(side=side, steps=steps)
+    label_kw = dict(side=side, steps=steps, r0sq=r0sq)
     res = active_sweep(rounds=rounds, per_round=per_round, first=first, pool=pool, seed=seed,
                        label_kw=label_kw, train_kw=dict(steps=train_steps, lr=2e-3, batch=256,
                                                         decay=3))
@@ -717,7 +717,7 @@ def boundary_gain(rounds=3, per_round=128, first=256, pool=8192, seed=0, side=25
     uni = draw_points(rounds * per_round, seed + 777)
     uv, ub, _ = solver_labels(uni, seed0=900_000, **label_kw)
     slow = np.quantile(uv, 0.1)
-    out = {"side": side, "steps_per_point": steps, "first": first, "rounds": rounds,
+    out = {"side": side, "steps_per_point": steps, "r0sq": r0sq, "first": first, "rounds": rounds,
            "per_round": per_round,
            "initial_branched_fraction": float((res["labels"][:first, 1] >= 1).mean()),
            "uniform_branched_fraction": float((ub >= 1).mean()),

@@ -10,6 +10,8 @@ import pytest
 import oracle
 from paper_1301_5058_gb300 import workloads as W
 
+from _layout import natural
+
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
@@ -174,13 +176,13 @@ def test_create_with_caller_buffers(cx, prec):
     with cx.Sim(nx, ny, 1.0, seed=seed, handle=h, **params) as own, \
             cx.Sim(nx, ny, 1.0, seed=seed, **params) as ref:
         torch.cuda.synchronize()
-        assert np.array_equal(s[:, :nx].cpu().numpy(), ref.field(cx.CX_FIELD_SIGMA, npd))
+        assert np.array_equal(natural(s, nx), ref.field(cx.CX_FIELD_SIGMA, npd))
         for sim in (own, ref):
             sim.step(37)
         for w in (cx.CX_FIELD_B, cx.CX_FIELD_N):
             assert np.array_equal(own.field(w, npd), ref.field(w, npd))
         cur = own.field(cx.CX_FIELD_B, npd)
-        held = [b[q, :, :nx].cpu().numpy() for q in (0, 1)]
+        held = [natural(b[q], nx) for q in (0, 1)]
         assert any(np.array_equal(cur, x) for x in held)
 
 
@@ -201,3 +203,10 @@ def test_create_with_caller_buffers_rejects_bad_layouts(cx):
         with pytest.raises(cx.CxError) as e:
             cx.cx_create_with_buffers(g, p, 0, b, n, s, pt)
         assert e.value.code == cx.CX_ERR_INVALID_ARG
+    # FP64 rows of 66 elements are 16-byte sized but not whole groups of four
+    p64 = cx.cx_params_default(**dict(params, precision=0))
+    t64 = torch.zeros((6, ny, 68), dtype=torch.float64, device="cuda")
+    q = [t64[i].data_ptr() for i in range(6)]
+    with pytest.raises(cx.CxError) as e:
+        cx.cx_create_with_buffers(g, p64, 0, [q[0], q[1]], [q[2], q[3]], q[4], 66)
+    assert e.value.code == cx.CX_ERR_INVALID_ARG

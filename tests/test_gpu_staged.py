@@ -7,6 +7,8 @@ import pytest
 
 from paper_1301_5058_gb300 import workloads as W
 
+from _layout import natural
+
 pytestmark = pytest.mark.gpu
 
 
@@ -107,7 +109,7 @@ def test_staged_state_into_caller_buffers(cx):
         own.stage_state(fb, fn)
         own.commit_state()
         cx.cx_synchronize(own.h)
-        held = [b[q, :, :nx].cpu().numpy() for q in (0, 1)]
+        held = [natural(b[q], nx) for q in (0, 1)]
         assert any(np.array_equal(fb, x) for x in held)
         for sim in (own, ref):
             sim.step(10)
