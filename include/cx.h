@@ -363,34 +363,54 @@ int cx_batch_polar_profile(cx_batch *b, int32_t index, double radius, int32_t ns
 
 /* ---- surrogate network ----------------------------------------------------
  *
- * An MLP 4 -> 256 -> 256 -> 2 with tanh hidden units that maps a sweep point
- * (normalised n0, chi0, sigma0, a) to normalised morphology labels
- * (envelope velocity, branch count), trained on data the solver produces.
- * The 256 x 256 layer runs on the tensor cores with bf16 operands and FP32
- * accumulation; everything else is FP32.  Parameters are FP32, packed as
- * W1 (256 x 4, row-major), b1 (256), W2 (256 x 256), b2 (256), W3 (2 x 256),
- * b3 (2): CX_MLP_PARAMS floats.  Loss = sum (Y - T)^2 / (2 B).  The paper
- * has no counterpart: the network only proposes and pre-screens sweep
- * points; every reported label comes from the solver. */
+ * An ensemble of E independent MLPs 4 -> 256 -> 256 -> 2 with tanh hidden
+ * units that map a sweep point (normalised n0, chi0, sigma0, a) to
+ * normalised morphology labels (envelope velocity, branch count), trained
+ * on data the solver produces.  The 256 x 256 layer and its two backward
+ * products run on the tensor cores (tcgen05, bf16 operands, FP32
+ * accumulation in tensor memory); everything else is FP32.  One member's
+ * parameters are FP32, packed as W1 (256 x 4, row-major), b1 (256), W2
+ * (256 x 256), b2 (256), W3 (2 x 256), b3 (2): CX_MLP_PARAMS floats; the
+ * members' blocks follow one another (member-major).  Loss = sum (Y - T)^2
+ * / (2 B).  Member e of an E-member network computes, bit for bit, what a
+ * one-member network with member e's parameters and data computes.  The
+ * paper has no counterpart: the network only proposes and pre-screens sweep
+ * points; every reported label comes from the solver.
+ *
+ * Every call below is synchronous and returns CX_ERR_TIMEOUT if a bounded
+ * device-side wait for the tensor cores ran out (the results of that call
+ * are then undefined; the network stays usable).  The environment variable
+ * CX_MMA_WAIT_LIMIT, read when a network is created, sets the number of
+ * polls of that wait (default 2^22). */
 #define CX_MLP_PARAMS 67586
 typedef struct cx_mlp cx_mlp;
 
-/* Allocate a network for batches of up to max_batch rows (1..2^20); the
- * parameters start at zero (set them with cx_mlp_set_params). */
+/* Allocate a network of `members` (1..64) members for batches of up to
+ * max_batch rows (1..2^20); the parameters start at zero (set them with
+ * cx_mlp_set_params).  Device memory: about members x max_batch x 5.7 KB
+ * (the activations of the backward pass). */
+int cx_mlp_create_members(int32_t max_batch, int32_t members, cx_mlp **out);
+/* cx_mlp_create_members(max_batch, 1, out). */
 int cx_mlp_create(int32_t max_batch, cx_mlp **out);
-/* Set / read all parameters (count == CX_MLP_PARAMS); setting them also
- * resets the optimiser state. */
+/* Number of members (0 for NULL). */
+int32_t cx_mlp_members(const cx_mlp *m);
+/* Set / read all parameters (count == members x CX_MLP_PARAMS); setting
+ * them also resets the optimiser state. */
 int cx_mlp_set_params(cx_mlp *m, const float *host, size_t count);
 int cx_mlp_get_params(cx_mlp *m, float *host, size_t count);
-/* y (batch x 2) = network(x (batch x 4)), host arrays.  Synchronous. */
+/* Every member on the same inputs: x (batch x 4) -> y (members x batch x 2),
+ * host arrays. */
 int cx_mlp_forward(cx_mlp *m, const float *x, int32_t batch, float *y);
-/* Loss and its gradient (CX_MLP_PARAMS floats, same packing) on one batch. */
+/* Loss and gradient of every member on the same batch (x, t): grad receives
+ * members x CX_MLP_PARAMS floats (same packing), loss (optional) members
+ * doubles. */
 int cx_mlp_gradient(cx_mlp *m, const float *x, const float *t, int32_t batch, float *grad,
                     double *loss);
-/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) over
- * minibatches of `batch` consecutive rows of the n-row set (x, t), taken
- * cyclically (shuffle the rows beforehand).  loss_out (optional, `steps`
- * doubles) receives each step's minibatch loss.  Synchronous. */
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) of every
+ * member over minibatches of `batch` consecutive rows of its own n-row set,
+ * taken cyclically (shuffle the rows beforehand): x is members x n x 4, t
+ * members x n x 2 (member-major).  loss_out (optional, members x steps
+ * doubles) receives each member's minibatch losses. */
 int cx_mlp_train(cx_mlp *m, const float *x, const float *t, int32_t n, int32_t batch,
                  int32_t steps, float lr, double *loss_out);
 /* Free the network.  NULL is a no-op. */

@@ -129,11 +129,12 @@ _SIGNATURES = {
     "cx_batch_polar_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                               _P]),
     "cx_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P)]),
+    "cx_mlp_create_members": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "cx_mlp_members": (ctypes.c_int32, [_P]),
     "cx_mlp_set_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cx_mlp_get_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cx_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
-    "cx_mlp_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P,
-                                       ctypes.POINTER(ctypes.c_double)]),
+    "cx_mlp_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, _P]),
     "cx_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_float, _P]),
     "cx_mlp_destroy": (None, [_P]),
@@ -431,44 +432,60 @@ def _f32(a, cols):
 
 
 class Mlp:
-    """The surrogate network (include/cx.h, cx_mlp_*)."""
+    """The surrogate network (include/cx.h, cx_mlp_*): `members` independent
+    networks trained and evaluated together.  With one member the arrays
+    have no member axis."""
 
-    def __init__(self, max_batch: int, params=None):
+    def __init__(self, max_batch: int, params=None, members: int = 1):
         h = _P()
-        _check(lib().cx_mlp_create(max_batch, ctypes.byref(h)))
+        _check(lib().cx_mlp_create_members(max_batch, members, ctypes.byref(h)))
         self.h = h.value
+        self.members = members
         if params is not None:
             self.set_params(params)
 
+    def _squeeze(self, a):
+        return a[0] if self.members == 1 else a
+
     def set_params(self, theta):
-        theta = np.ascontiguousarray(theta, np.float32)
+        theta = np.ascontiguousarray(theta, np.float32).reshape(-1)
         _check(lib().cx_mlp_set_params(self.h, theta.ctypes.data, theta.size))
 
     def params(self) -> np.ndarray:
-        out = np.empty(CX_MLP_PARAMS, np.float32)
+        out = np.empty((self.members, CX_MLP_PARAMS), np.float32)
         _check(lib().cx_mlp_get_params(self.h, out.ctypes.data, out.size))
-        return out
+        return self._squeeze(out)
 
     def forward(self, x) -> np.ndarray:
+        """(n, 2) outputs, or (members, n, 2); x (n, 4) is shared."""
         x = _f32(x, 4)
-        y = np.empty((x.shape[0], 2), np.float32)
+        y = np.empty((self.members, x.shape[0], 2), np.float32)
         _check(lib().cx_mlp_forward(self.h, x.ctypes.data, x.shape[0], y.ctypes.data))
-        return y
+        return self._squeeze(y)
 
     def gradient(self, x, t):
+        """(loss, gradient) of every member on the shared batch (x, t)."""
         x, t = _f32(x, 4), _f32(t, 2)
-        g = np.empty(CX_MLP_PARAMS, np.float32)
-        loss = ctypes.c_double()
+        g = np.empty((self.members, CX_MLP_PARAMS), np.float32)
+        loss = np.empty(self.members, np.float64)
         _check(lib().cx_mlp_gradient(self.h, x.ctypes.data, t.ctypes.data, x.shape[0],
-                                     g.ctypes.data, ctypes.byref(loss)))
-        return loss.value, g
+                                     g.ctypes.data, loss.ctypes.data))
+        return (float(loss[0]), g[0]) if self.members == 1 else (loss, g)
 
     def train(self, x, t, batch: int, steps: int, lr: float) -> np.ndarray:
-        x, t = _f32(x, 4), _f32(t, 2)
-        losses = np.empty(steps, np.float64)
-        _check(lib().cx_mlp_train(self.h, x.ctypes.data, t.ctypes.data, x.shape[0], batch, steps,
+        """x (n, 4) and t (n, 2), or one set per member ((members, n, 4) and
+        (members, n, 2)); returns the step losses, (steps,) or (members, steps)."""
+        x = np.ascontiguousarray(x, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        if x.ndim == 2:
+            x = np.broadcast_to(x, (self.members,) + x.shape).copy()
+            t = np.broadcast_to(t, (self.members,) + t.shape).copy()
+        if x.shape[0] != self.members or x.shape[2] != 4 or t.shape != x.shape[:2] + (2,):
+            raise ValueError("expected (members, n, 4) inputs and (members, n, 2) targets")
+        losses = np.empty((self.members, steps), np.float64)
+        _check(lib().cx_mlp_train(self.h, x.ctypes.data, t.ctypes.data, x.shape[1], batch, steps,
                                   lr, losses.ctypes.data))
-        return losses
+        return self._squeeze(losses)
 
     def close(self):
         if getattr(self, "h", None):

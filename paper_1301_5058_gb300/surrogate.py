@@ -168,14 +168,22 @@ def init_params(seed: int) -> np.ndarray:
 
 
 class Surrogate:
-    """Network + output scaling.  predict() returns labels in solver units."""
+    """Network + output scaling.  predict() returns labels in solver units.
+    members > 1: that many networks (initial weights from seeds seed,
+    seed + 17, seed + 34, ...) trained together on the same labels, each on
+    its own row order; predict() then returns (members, n, 2)."""
 
-    def __init__(self, seed=0, max_batch=8192):
-        self.net = cx.Mlp(max_batch, init_params(seed))
+    def __init__(self, seed=0, max_batch=8192, members=1):
+        self.seeds = [seed + 17 * k for k in range(members)]
+        self.members = members
+        self.net = cx.Mlp(max_batch, self._initial(), members=members)
         self.max_batch = max_batch
         self.seed = seed
         self.mean = np.zeros(2)
         self.scale = np.ones(2)
+
+    def _initial(self):
+        return np.concatenate([init_params(s) for s in self.seeds])
 
     def fit(self, points, labels, steps=3000, lr=1e-3, batch=256, reinit=True, decay=0,
             schedule="halve"):
@@ -183,34 +191,38 @@ class Surrogate:
         into decay + 1 equal chunks and the rows reshuffled from one chunk to
         the next (the optimiser state carries over); the rate is halved from
         chunk to chunk (schedule "halve") or follows a cosine from lr down to
-        lr / (2 (decay + 1)) ("cosine")."""
+        lr / (2 (decay + 1)) ("cosine").  Returns the step losses ((steps,),
+        or (members, steps))."""
         X = encode(points)
         Y = np.asarray(labels, np.float64)
         self.mean = Y.mean(0)
         self.scale = Y.std(0) + 1e-12
         T = ((Y - self.mean) / self.scale).astype(np.float32)
-        rng = np.random.default_rng(self.seed + len(X))
+        rngs = [np.random.default_rng(s + len(X)) for s in self.seeds]
         batch = min(batch, len(X))
         if reinit:
-            self.net.set_params(init_params(self.seed))
+            self.net.set_params(self._initial())
         losses = []
         chunk = max(1, steps // (decay + 1))
         for k in range(decay + 1):
-            perm = rng.permutation(len(X))
+            perms = [r.permutation(len(X)) for r in rngs]
             n = chunk if k < decay else steps - chunk * decay
             if n > 0:
                 rate = lr * 0.5 ** k if schedule == "halve" else \
                     lr * 0.5 * (1.0 + math.cos(math.pi * (k + 0.5) / (decay + 1)))
-                losses.append(self.net.train(X[perm], T[perm], batch, n, rate))
-        return np.concatenate(losses)
+                xs = np.stack([X[p] for p in perms])
+                ts = np.stack([T[p] for p in perms])
+                losses.append(self.net.train(xs, ts, batch, n, rate))
+        return np.concatenate(losses, axis=-1)
 
     def predict(self, points) -> np.ndarray:
         X = encode(points)
-        out = np.empty((len(X), 2))
+        out = np.empty((self.members, len(X), 2))
         c = self.max_batch
         for s in range(0, len(X), c):
-            out[s:s + c] = self.net.forward(X[s:s + c])
-        return out * self.scale + self.mean
+            out[:, s:s + c] = self.net.forward(X[s:s + c]).reshape(self.members, -1, 2)
+        out = out * self.scale + self.mean
+        return out[0] if self.members == 1 else out
 
     def close(self):
         self.net.close()
@@ -296,33 +308,34 @@ def demo(side=256, steps=4000, n_train=256, n_test=128, train_steps=3000, seed=0
 
 class Ensemble:
     """Several networks trained on log(velocity) from different initial
-    weights; a point is accepted without a solver run when the members agree
-    to within `agree` (relative spread of the predicted velocity)."""
+    weights (the members of one network handle, trained together); a point
+    is accepted without a solver run when the members agree to within
+    `agree` (relative spread of the predicted velocity)."""
 
     def __init__(self, members=4, seed=0, max_batch=8192):
-        self.models = [Surrogate(seed + 17 * k, max_batch) for k in range(members)]
+        self.model = Surrogate(seed, max_batch, members=members)
+        self.members = members
+
+    def fit_labels(self, points, labels, **kw):
+        return self.model.fit(points, labels, **kw)
 
     def fit(self, points, velocity, **kw):
-        """Train the members concurrently: each network has its own stream and
-        buffers, and the library calls release the interpreter lock, so the
-        members' small kernels overlap on the GPU; the results do not depend
-        on the interleaving."""
-        from concurrent.futures import ThreadPoolExecutor
         lv = np.log(np.maximum(np.asarray(velocity, np.float64), 1e-12))
-        y = np.stack([lv, np.zeros_like(lv)], 1)
-        with ThreadPoolExecutor(max_workers=len(self.models)) as ex:
-            return list(ex.map(lambda m: m.fit(points, y, **kw), self.models))
+        return self.fit_labels(points, np.stack([lv, np.zeros_like(lv)], 1), **kw)
+
+    def member_outputs(self, points):
+        """First output of every member, (members, n)."""
+        p = self.model.predict(points)
+        return (p[None] if self.members == 1 else p)[..., 0]
 
     def predict(self, points):
-        lv = np.stack([m.predict(points)[:, 0] for m in self.models], 0)
-        v = np.exp(lv)
+        v = np.exp(self.member_outputs(points))
         mean = v.mean(0)
         spread = (v.max(0) - v.min(0)) / np.maximum(mean, 1e-30)
         return mean, spread
 
     def close(self):
-        for m in self.models:
-            m.close()
+        self.model.close()
 
 
 def poly_features(X, degree=3) -> np.ndarray:
@@ -358,17 +371,14 @@ class Screen:
         return poly_features(X, self.degree) @ self.coef
 
     def _net_log(self, points):
-        return np.mean([m.predict(points)[:, 0] for m in self.ens.models], 0)
+        return self.ens.member_outputs(points).mean(0)
 
     def fit(self, points, velocity, **kw):
         X = encode(points).astype(np.float64)
         y = np.log(np.maximum(np.asarray(velocity, np.float64), 1e-12))
         self.coef, *_ = np.linalg.lstsq(poly_features(X, self.degree), y, rcond=None)
         r = y - self._base_log(X)
-        from concurrent.futures import ThreadPoolExecutor
-        t = np.stack([r, np.zeros_like(r)], 1)
-        with ThreadPoolExecutor(max_workers=len(self.ens.models)) as ex:
-            list(ex.map(lambda m: m.fit(points, t, **kw), self.ens.models))
+        self.ens.fit_labels(points, np.stack([r, np.zeros_like(r)], 1), **kw)
         self.X = X
         self.res = y - self._base_log(X) - self._net_log(points)
         return self

@@ -57,6 +57,50 @@ def test_gradient_matches_oracle(cx, batch):
         assert err <= 1e-3, (name, err)
 
 
+def test_members_compute_what_single_networks_compute(cx):
+    # three members with their own parameters and training rows: forward,
+    # gradient and 40 Adam steps equal, bit for bit, one-member networks
+    # given the same parameters and rows (batch 200: two 128-row tiles, one
+    # of them ragged)
+    E, n, batch = 3, 600, 200
+    thetas = [_theta(10 + k) for k in range(E)]
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (E, n, 4)).astype(np.float32)
+    T = rng.normal(size=(E, n, 2)).astype(np.float32)
+    with cx.Mlp(1024, np.stack(thetas), members=E) as net:
+        y = net.forward(X[0])
+        loss, g = net.gradient(X[0, :batch], T[0, :batch])
+        losses = net.train(X, T, batch, 40, 1e-3)
+        p = net.params()
+    assert y.shape == (E, n, 2) and g.shape == (E, 67586) and losses.shape == (E, 40)
+    for k in range(E):
+        with cx.Mlp(1024, thetas[k]) as one:
+            assert np.array_equal(one.forward(X[0]), y[k])
+            l1, g1 = one.gradient(X[0, :batch], T[0, :batch])
+            assert l1 == loss[k] and np.array_equal(g1, g[k])
+            assert np.array_equal(one.train(X[k], T[k], batch, 40, 1e-3), losses[k])
+            assert np.array_equal(one.params(), p[k])
+
+
+def test_tensor_core_wait_timeout_is_reported(cx, monkeypatch):
+    # failure detection without a GPU fault: a wait limit of 0 makes every
+    # tile's first completion wait give up at once; the tile then waits
+    # (bounded) for its products, releases its tensor memory and returns,
+    # and the host reports CX_ERR_TIMEOUT
+    theta = _theta(5)
+    x = np.random.default_rng(0).uniform(-1, 1, (300, 4)).astype(np.float32)
+    monkeypatch.setenv("CX_MMA_WAIT_LIMIT", "0")
+    with cx.Mlp(512, theta) as net:
+        with pytest.raises(cx.CxError) as e:
+            net.forward(x)
+        assert e.value.code == cx.CX_ERR_TIMEOUT
+    monkeypatch.delenv("CX_MMA_WAIT_LIMIT")
+    with cx.Mlp(512, theta) as net:                # the device still works
+        y = net.forward(x)
+    oy, _ = omlp.forward(theta.astype(np.float64), x.astype(np.float64), rounding=True)
+    assert np.linalg.norm(y - oy) <= 1e-4 * np.linalg.norm(oy)
+
+
 def test_training_fits_a_smooth_map(cx):
     rng = np.random.default_rng(0)
     X = rng.uniform(-1, 1, (4096, 4)).astype(np.float32)
