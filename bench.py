@@ -96,11 +96,13 @@ def parse():
                          "default: the library's (2 for FP32, 1 for FP64)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="grid", choices=["grid", "sweep", "validated"],
+    ap.add_argument("--workload", default="grid",
+                    choices=["grid", "sweep", "validated", "screen-training"],
                     help="grid: the 16384^2 single grid; sweep: the batched parameter sweep; "
                          "validated: validated sweep points/hour with the learned screen "
                          "(solver-labelled training runs at 1024^2, held-out points on the "
-                         "512..2048 size mix; several minutes)")
+                         "512..2048 size mix; several minutes); screen-training: Adam steps "
+                         "of the screen's 8-member network (batch 256)")
     ap.add_argument("--n-train", type=int, default=8192, help="validated: training runs")
     ap.add_argument("--n-test", type=int, default=1024, help="validated: held-out points")
     ap.add_argument("--count", type=int, default=512, help="sweep instances")
@@ -594,6 +596,33 @@ RECORDS = {
 }
 
 
+def screen_training_record(args, members=8, rows=8192, batch=256):
+    """Adam steps of the screen's network (members trained together, each on
+    its own rows of random data): `warmup` steps, then `steps` steps timed by
+    the host clock around the library's synchronous training call (the
+    network runs on its own stream)."""
+    import numpy as np
+    import paper_1301_5058_gb300 as cx
+    from paper_1301_5058_gb300 import surrogate
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1, 1, (members, rows, 4)).astype(np.float32)
+    T = rng.normal(size=(members, rows, 2)).astype(np.float32)
+    theta = np.concatenate([surrogate.init_params(k) for k in range(members)])
+    with cx.Mlp(rows, theta, members=members) as net:
+        net.train(X, T, batch, max(args.warmup, 1), 1e-3)
+        t0 = time.perf_counter()
+        losses = net.train(X, T, batch, args.steps, 1e-3)
+        sec = time.perf_counter() - t0
+    return {"metric": "screen training steps/s", "value": args.steps / sec, "unit": "steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 products, f32 accumulation", "data": "synthetic",
+            "gpu_launches": 4 * args.steps,
+            "config": {"workload": f"surrogate network 4-256-256-2, {members} members trained "
+                                   f"together, minibatch {batch} of {rows} rows each"},
+            "final_loss": float(np.mean(losses[:, -1]))}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -618,6 +647,11 @@ def main():
                                                  "sweep box, sides 512..2048, 20000 steps per "
                                                  "point"},
                           "validated": v, "clocks": clk.summary()}))
+        return
+    if args.workload == "screen-training":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(screen_training_record(args)))
         return
     if args.workload == "sweep":
         import torch

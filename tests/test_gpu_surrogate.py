@@ -82,6 +82,18 @@ def test_members_compute_what_single_networks_compute(cx):
             assert np.array_equal(one.params(), p[k])
 
 
+def test_forward_at_the_screens_batch_matches_oracle(cx):
+    # the screen evaluates candidates 8192 at a time: 64 row tiles per member
+    thetas = [_theta(20 + k) for k in range(2)]
+    x = np.random.default_rng(7).uniform(-1, 1, (8192, 4)).astype(np.float32)
+    with cx.Mlp(8192, np.stack(thetas), members=2) as net:
+        y = net.forward(x)
+    for k in range(2):
+        oy, _ = omlp.forward(thetas[k].astype(np.float64), x.astype(np.float64), rounding=True)
+        assert np.linalg.norm(y[k] - oy) <= 1e-4 * np.linalg.norm(oy)
+        assert np.max(np.abs(y[k] - oy)) <= 1e-3 * np.max(np.abs(oy))
+
+
 def test_tensor_core_wait_timeout_is_reported(cx, monkeypatch):
     # failure detection without a GPU fault: a wait limit of 0 makes every
     # tile's first completion wait give up at once; the tile then waits
