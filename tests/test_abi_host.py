@@ -185,3 +185,22 @@ def test_batch_create_validates_before_any_device_call(cx):
                     (cx.lib().cx_batch_set_tuning, (None, 32, 0, 0, 0))):
         assert f(*args) == cx.CX_ERR_INVALID_ARG
     cx.lib().cx_batch_destroy(None)
+
+
+def test_network_create_and_calls_validate_before_any_device_call(cx):
+    import ctypes
+    L = cx.lib()
+    h = ctypes.c_void_p()
+    for max_batch, members in ((0, 1), (1 << 20 | 1, 1), (64, 0), (64, 65)):
+        assert L.cx_mlp_create_members(max_batch, members, ctypes.byref(h)) == cx.CX_ERR_INVALID_ARG
+        assert h.value is None
+    assert L.cx_mlp_create(0, ctypes.byref(h)) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_create_members(64, 2, None) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_members(None) == 0
+    buf = (ctypes.c_float * 8)()
+    assert L.cx_mlp_forward(None, buf, 1, buf) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_gradient(None, buf, buf, 1, buf, None) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_train(None, buf, buf, 1, 1, 1, 1e-3, None) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_set_params(None, buf, 8) == cx.CX_ERR_INVALID_ARG
+    assert L.cx_mlp_get_params(None, buf, 8) == cx.CX_ERR_INVALID_ARG
+    L.cx_mlp_destroy(None)

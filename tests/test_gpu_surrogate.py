@@ -82,6 +82,37 @@ def test_members_compute_what_single_networks_compute(cx):
             assert np.array_equal(one.params(), p[k])
 
 
+@pytest.mark.parametrize("batch,cap", [(1, 1), (128, 128), (129, 256)])
+def test_gradient_edge_batches_match_oracle(cx, batch, cap):
+    # one valid row in a 128-row tile; a batch at exactly the capacity; one
+    # row into a second tile
+    theta = _theta(batch + 7)
+    rng = np.random.default_rng(batch)
+    X = rng.uniform(-1, 1, (batch, 4)).astype(np.float32)
+    T = rng.normal(size=(batch, 2)).astype(np.float32)
+    with cx.Mlp(cap, theta) as net:
+        loss, g = net.gradient(X, T)
+    oloss, og = omlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64),
+                                   T.astype(np.float64), rounding=True)
+    assert loss == pytest.approx(oloss, rel=1e-4)
+    gb, ob = _blocks(g), _blocks(og)
+    for name in gb:
+        err = np.linalg.norm(gb[name] - ob[name]) / max(np.linalg.norm(ob[name]), 1e-30)
+        assert err <= 1e-3, (name, err)
+
+
+def test_sixty_four_members(cx):
+    # the largest ensemble: every member's forward equals its own one-member network
+    thetas = np.stack([_theta(100 + k) for k in range(64)])
+    x = np.random.default_rng(2).uniform(-1, 1, (200, 4)).astype(np.float32)
+    with cx.Mlp(256, thetas, members=64) as net:
+        assert cx.lib().cx_mlp_members(net.h) == 64
+        y = net.forward(x)
+    for k in (0, 1, 37, 63):
+        with cx.Mlp(256, thetas[k]) as one:
+            assert np.array_equal(one.forward(x), y[k])
+
+
 def test_forward_at_the_screens_batch_matches_oracle(cx):
     # the screen evaluates candidates 8192 at a time: 64 row tiles per member
     thetas = [_theta(20 + k) for k in range(2)]
