@@ -182,6 +182,47 @@ def kernel_traffic(prec, name, nx, ny, scheme, noise):
     return None
 
 
+def sweep_issue_count(count, tuning):
+    """ncu warp instructions per launch of the two-stage batch kernel on the
+    512-instance sweep, recorded with its traffic (null otherwise)."""
+    rec = _traffic_record("batch_fused_kernel")
+    if rec is None or count != 512:
+        return None
+    entry = rec.get("f32", {})
+    if any(tuning.get(k) != v for k, v in entry.get("tuning", {}).items()):
+        return None
+    return entry.get("warp_instructions_per_launch")
+
+
+def kernel_issue_count(prec, name, nx, ny, scheme, noise):
+    """ncu warp instructions per launch of kernel `name` on an nx x ny grid,
+    recorded with the traffic (null when not recorded or the sources changed)."""
+    rec = _traffic_record(name)
+    if rec is None or nx != ny:
+        return None
+    entries = rec.get(prec, [])
+    for entry in entries if isinstance(entries, list) else [entries]:
+        if (entry.get("scheme"), entry.get("noise")) == (scheme, noise):
+            return entry.get(f"warp_instructions_per_launch_{nx}sq")
+    return None
+
+
+def issue_roofline(warp_inst_per_launch, cell_updates_per_launch, rate, sm_mhz):
+    """Instruction-issue roofline of a launch: its warp instructions per
+    cell-update times the measured cell-update rate, against one warp
+    instruction per scheduler and clock (4 schedulers per SM)."""
+    if not warp_inst_per_launch:
+        return None
+    w = warp_inst_per_launch / cell_updates_per_launch
+    peak = 4 * SMS * sm_mhz * 1e6
+    return {"bound": "issue", "unit": "warp instructions/s",
+            "warp_instructions_per_cell_update": w, "achieved": w * rate, "peak": peak,
+            "frac": w * rate / peak,
+            "peak_kind": f"4 schedulers x {SMS} SMs x {sm_mhz:.0f} MHz (median SM clock of "
+                         "the timed region), one warp instruction each per clock",
+            "source": "ncu smsp__inst_executed.sum per launch, recorded with the traffic"}
+
+
 def sweep_traffic(count, tuning):
     """ncu DRAM bytes per launch of the two-stage batch kernel on the
     512-instance sweep, if recorded for this tuning and the current sources
@@ -460,6 +501,10 @@ def grid_line(spec, r, K, world, peak, peak_kind, alu_peaks):
         roofline = dict(hbm, alu_fp32=alu)
         if tb == 2:
             roofline["limiter"] = LIMITER_TB2 if scheme == "euler" else LIMITER_HEUN
+            clock = r["clocks"].get("sm_mhz") or sm_mhz
+            roofline["issue"] = issue_roofline(
+                kernel_issue_count(prec, kernel, cfg["nx"], cfg["ny"], scheme, noise),
+                cells * (2 if scheme == "euler" else 1), rate, clock)
     return {
         "value": units / r["elapsed"],
         "unit": "cell-updates/s",
@@ -860,7 +905,10 @@ def sweep_record(args):
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": sweep_traffic(args.count, tuning),
                      "kernel": "batch_fused_kernel" if depth == 2 else "batch_step_kernel",
-                     "algorithmic_bytes_per_cell": bpc},
+                     "algorithmic_bytes_per_cell": bpc,
+                     "issue": issue_roofline(sweep_issue_count(args.count, tuning) if depth == 2
+                                             else None, 2 * cells, cells / (kernel_s / (K * S)),
+                                             clk.summary().get("sm_mhz") or 2070.0)},
         "gpu_launches": K * (launches_per_window("euler", depth, S) + 2),
         "clocks": clk.summary(),
     }

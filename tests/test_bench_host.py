@@ -74,3 +74,24 @@ def test_sweep_traffic_record_applies_only_to_its_tuning(tmp_path, monkeypatch):
     other = 32 if tuning["tile_rows"] != 32 else 64
     assert bench.sweep_traffic(512, dict(tuning, tile_rows=other)) is None  # other tiles
     assert bench.sweep_traffic(512, dict(tuning, time_block=1)) is None    # one stage per pass
+
+
+def test_issue_roofline_from_the_recorded_instruction_counts(tmp_path, monkeypatch):
+    root = _scratch_root(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    rec = json.load(open(root / "profiles" / "fused_kernel_traffic.json"))
+    want = {(e["scheme"], e["noise"]): e["warp_instructions_per_launch_16384sq"] for e in rec["f32"]}
+    assert bench.kernel_issue_count("f32", "fused_kernel", 16384, 16384, "euler", "static") == \
+        want[("euler", "static")]
+    assert bench.kernel_issue_count("f32", "fused_kernel", 4096, 4096, "euler", "static") is None
+    # one warp instruction per scheduler and clock: 4 x 152 SMs x 2000 MHz = 1.216e12 / s
+    r = bench.issue_roofline(2000, 1000, 3e11, 2000.0)
+    assert r["warp_instructions_per_cell_update"] == 2.0
+    assert abs(r["peak"] - 1.216e12) < 1.0 and abs(r["frac"] - 6e11 / 1.216e12) < 1e-12
+    assert bench.issue_roofline(None, 1000, 3e11, 2000.0) is None
+    batch = json.load(open(root / "profiles" / "batch_fused_kernel_traffic.json"))["f32"]
+    assert bench.sweep_issue_count(512, dict(batch["tuning"])) == batch["warp_instructions_per_launch"]
+    src = root / "paper_1301_5058_gb300" / "csrc" / "cx_stencil.cuh"
+    src.write_text(src.read_text() + "\n// edited\n")
+    assert bench.kernel_issue_count("f32", "fused_kernel", 16384, 16384, "euler", "static") is None
+    assert bench.sweep_issue_count(512, dict(batch["tuning"])) is None
