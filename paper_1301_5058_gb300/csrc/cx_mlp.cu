@@ -238,10 +238,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
 }
 
-}  // namespace
-
-namespace {
-
 // Device view of an E-member network; member e's arrays start at e times
 // the per-member sizes (NPARAM, H * H, Bmax * H, Bmax * NO, Bmax).
 struct NetView {
