@@ -297,8 +297,9 @@ int cx_batch_create(int32_t count, const cx_grid *grids, const cx_params *params
 int cx_batch_set_stream(cx_batch *b, void *stream);
 
 /* Performance knobs, none of which changes any result bit:
- *   tile_rows   rows per tile of the step kernel (1..4096, default 32; the
- *               tiles of both depths);
+ *   tile_rows   rows per tile of the step kernel (1..4096; the tiles of
+ *               both depths; default 128 for FP32 batches, which take two
+ *               stages per pass, 32 for FP64 ones);
  *   graph_steps steps captured per CUDA graph and replayed (0: plain
  *               launches; rounded up to even for Euler; default 64);
  *   group_bytes if > 0, instances are cut into consecutive groups whose

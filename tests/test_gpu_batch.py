@@ -173,9 +173,10 @@ def test_resident_barrier_timeout_is_reported(cx, monkeypatch):
 
 
 def test_batch_time_block_default_and_validation(cx):
-    for prec, default in ((1, 2), (0, 1)):
+    for prec, default, rows in ((1, 2, 128), (0, 1, 32)):
         with cx.Batch(specs(prec, 0, sizes=[(64, 48), (7, 5)])) as bt:
             assert cx.cx_batch_get_time_block(bt.h) == default
+            assert cx.cx_batch_get_tuning(bt.h)[0] == rows   # default tile height by depth
             for bad in (0, 3):
                 with pytest.raises(cx.CxError) as e:
                     cx.cx_batch_set_time_block(bt.h, bad)
