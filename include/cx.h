@@ -245,8 +245,10 @@ int cx_set_step(cx_ctx *c, int64_t step);
  * ceil(ny/rows) <= 65535, or 0 for the automatic height; a performance
  * knob that the autotuner sets.  The result is bit-identical for every
  * value.  Automatic: 32 rows (64 with two stages per pass), or fewer on
- * small grids so that about four tiles per SM (eight with two stages) are
- * launched; cx_get_tile_rows reports the height in effect. */
+ * small grids so that about four tiles per SM are launched (sixteen
+ * one-warp tiles with two stages and static sigma, eight four-warp tiles
+ * with sigma redrawn per step); cx_get_tile_rows reports the height in
+ * effect. */
 int cx_set_tile_rows(cx_ctx *c, int32_t rows);
 int cx_get_tile_rows(cx_ctx *c, int32_t *rows);
 

@@ -28,7 +28,7 @@ BATCH_CANDIDATES = [(rows, graph, 0, 0, depth) for depth in (1, 2) for rows in (
                     for graph in (0, 64)]
 RESIDENT_CANDIDATES = [(rows, 0, group, res, 1) for rows in (4, 8, 16)
                        for group in (L2_BYTES // 2, L2_BYTES // 4) for res in (50, 200)]
-SINGLE_CANDIDATES = (8, 16, 32, 64, 128, 256)
+SINGLE_CANDIDATES = (2, 4, 8, 16, 32, 64, 128, 256)
 
 
 def cache_path() -> str:

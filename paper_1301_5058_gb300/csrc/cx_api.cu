@@ -317,12 +317,21 @@ int cx_dt_limit(const cx_grid *g, const cx_params *p, double *limit)
 // neighbour tiles), or fewer so that a smaller grid still launches about four
 // tiles per SM (eight with two stages, whose blocks hold fewer warps per SM)
 // instead of a handful of long, latency-bound marches.
+// Tall tiles amortise the halo rows a tile recomputes; enough tiles keep
+// every SM busy on small grids.  Per SM: four 512-column CTAs (one stage
+// per pass), sixteen 120-column one-warp CTAs (two stages, static sigma) or
+// eight 480-column four-warp CTAs (two stages, sigma drawn per step).  On
+// single FP32 grids with static sigma this picks 2, 4, 9 and 16 rows at
+// sides 512, 1024, 1536 and 2048, the fastest measured heights or within
+// 4 % of them (the earlier 480-column estimate picked 1, 3, 6 and 9 rows,
+// 18-49 % slower), and 64 rows at 16384^2.
 static int auto_tile_rows(const cx_ctx *c)
 {
     const bool two = c->time_block == 2;
-    const long long cols = two ? 480 : 512;
+    const bool one_warp = two && c->p.noise_mode != CX_NOISE_PER_STEP;
+    const long long cols = !two ? 512 : one_warp ? 120 : 480;
     const long long cap = two ? 64 : 32;
-    const long long per_sm = two ? 8 : 4;
+    const long long per_sm = !two ? 4 : one_warp ? 16 : 8;
     const long long tiles_x = ((long long)c->g.nx + cols - 1) / cols;
     const long long sms = c->num_sms;
     long long rows = ((long long)c->g.ny * tiles_x + per_sm * sms - 1) / (per_sm * sms);

@@ -129,19 +129,30 @@ def test_time_block_defaults_and_rejects_other_depths(cx):
 
 def test_automatic_tile_height_follows_the_depth(cx):
     # 8192^2 launches enough tiles for either cap; smaller grids get fewer
-    # rows so that about four tiles per SM are launched
+    # rows so that every SM gets its share of tiles: sixteen one-warp tiles
+    # of 120 columns (two stages, static sigma), eight four-warp tiles of 480
+    # columns (two stages, sigma drawn per step), four of 512 (one stage)
     params = dict(W.split(W.CONFIG0)[1], precision=1)
+    sms = 152
     with cx.Sim(8192, 8192, 1.0, seed=0, **params) as sim:
         cx.cx_set_time_block(sim.h, 1)
         assert cx.cx_get_tile_rows(sim.h) == 32
         cx.cx_set_time_block(sim.h, 2)
         assert cx.cx_get_tile_rows(sim.h) == 64
     with cx.Sim(4096, 4096, 1.0, seed=0, **params) as sim:
-        assert cx.cx_get_tile_rows(sim.h) == -(-4096 * 9 // (8 * 152))  # 9 tiles of 480 columns
+        assert cx.cx_get_tile_rows(sim.h) == -(-4096 * 35 // (16 * sms))  # 59
         cx.cx_set_tile_rows(sim.h, 17)
         assert cx.cx_get_tile_rows(sim.h) == 17
         cx.cx_set_tile_rows(sim.h, 0)
-        assert cx.cx_get_tile_rows(sim.h) == 31
+        assert cx.cx_get_tile_rows(sim.h) == 59
+        cx.cx_set_time_block(sim.h, 1)
+        assert cx.cx_get_tile_rows(sim.h) == 32   # 54 rows' worth of tiles, capped
+    for side, rows in ((512, 2), (1024, 4), (1536, 9), (2048, 16)):
+        with cx.Sim(side, side, 1.0, seed=0, **params) as sim:
+            assert cx.cx_get_tile_rows(sim.h) == rows
+    ps = dict(params, noise_mode=cx.CX_NOISE_PER_STEP)
+    with cx.Sim(4096, 4096, 1.0, seed=0, **ps) as sim:
+        assert cx.cx_get_tile_rows(sim.h) == -(-4096 * 9 // (8 * sms))  # 31
 
 
 def test_autotuner_picks_depth_and_height(cx, tmp_path, monkeypatch):
